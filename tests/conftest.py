@@ -1,0 +1,24 @@
+"""Shared pytest setup: markers, import path, and on-demand builds of the
+host-side C helpers (input generator and oracle)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: full-size workloads (minutes)")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _host_builds():
+    import graphgen
+    import oracle
+    graphgen.build()
+    oracle.build()
+    yield
