@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark: IMM seconds-to-seeds on one GB300 (plus sampling GTEPS and the
+roofline of the dominant kernel), through the C ABI.
+
+Default workload (one step = one whole IMM run, every hot-path step):
+  IC, R-MAT 1,048,576 vertices / 16,777,216 edges, p ~ U[0, 0.1] fp32,
+  k = 50, eps = 0.13, ell = 1, rng seed 2.
+The graph is resident in HBM before the timed region (value); the e2e number
+repeats the step through the same public calls from pinned host buffers, with
+the graph upload and the seed read-back inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+--impl reference times the oracle (plain single-threaded C on the host) on a
+bounded sample of the same workload and scales it to the whole run.
+Multi-GPU: replicas only (each rank runs the same workload on its own GPU);
+the timed region is bracketed by a barrier and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IMM seconds-to-seeds"
+WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--workload", choices=WORKLOADS, default="ic_u01_1m")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo", rank=self.rank, world_size=self.world)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def cpu_baseline(w, budget_s: float, full_sets: int, full_rounds_sets: list, k: int):
+    """Times the oracle on set ids 0..N-1 of the workload's stream (N grown
+    until ~budget_s of sampling) and one selection over them, then scales:
+    seconds = sampling s/set * sets the full run draws + selection s/member/round
+    * members the full run's selections scan."""
+    import oracle
+    g = w.graph
+    o = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+    t0 = time.perf_counter()
+    nsets = 0
+    step = 16
+    while time.perf_counter() - t0 < budget_s:
+        nsets += step
+        o.sample(nsets, w.seed)
+        step = min(step * 2, 4096)
+    t_sample = time.perf_counter() - t0
+    members = o.num_members
+    t1 = time.perf_counter()
+    o.select(k)
+    t_select = time.perf_counter() - t1
+    per_set = t_sample / nsets
+    per_member_select = t_select / max(members, 1)
+    # the full run selects once per sampling round plus once at the end, each
+    # over the whole stream at that point
+    avg_len = members / nsets
+    select_members = sum(s * avg_len for s in full_rounds_sets)
+    est = per_set * full_sets + per_member_select * select_members
+    return {
+        "seconds": est,
+        "sample": (f"oracle sampled set ids 0..{nsets - 1} ({members} members) in {t_sample:.1f} s and ran one "
+                   f"k={k} selection over them in {t_select:.2f} s; scaled to the full run's {full_sets} sets "
+                   f"and {len(full_rounds_sets)} selections"),
+        "cores": 1,
+        "sets_per_s": nsets / t_sample,
+    }
+
+
+def run_reference(args, dist: Dist):
+    import graphgen
+    if dist.rank != 0:
+        return
+    w = graphgen.plain_workload(args.workload)
+    # the stream size and selection schedule of the full run are fixed by the
+    # workload; they come from the oracle's own theta math and a short pilot
+    import oracle
+    g = w.graph
+    o = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+    prm = oracle.theta_params(g.n, w.k, w.epsilon, w.ell)
+    # pilot: coverage of a small stream estimates where the LB test fires
+    pilot = 200
+    o.sample(pilot, w.seed)
+    _, cov = o.select(w.k)
+    nF = g.n * cov / pilot
+    eps_p = 2 ** 0.5 * w.epsilon
+    import math
+    sets_rounds, lb = [], 1.0
+    for i in range(1, prm["rounds"] + 1):
+        x = g.n / 2.0 ** i
+        th = math.ceil(prm["lambda_prime"] / x)
+        sets_rounds.append(th)
+        if nF >= (1 + eps_p) * x:
+            lb = nF / (1 + eps_p)
+            break
+    theta = math.ceil(prm["lambda_star"] / lb)
+    full = max(theta, sets_rounds[-1] if sets_rounds else 0)
+    sets_rounds.append(full)
+    times = []
+    per_step_budget = max(2.0, args.cpu_sample_seconds / max(args.steps + args.warmup, 1))
+    res = None
+    for it in range(args.warmup + args.steps):
+        res = cpu_baseline(w, per_step_budget, full, sets_rounds, w.k)
+        if it >= args.warmup:
+            times.append(res["seconds"])
+    val = statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.desc, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": val, "unit": "s", "cores": res["cores"], "kind": "oracle", "sample": res["sample"]},
+        "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_2411_09473_gb300 import imm
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = graphgen.plain_workload(args.workload)
+    g = w.graph
+    ctx = imm.imm_create(device=dev, stream=stream)
+    imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, g.weight, g.model)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB > L2
+
+    def step():
+        return imm.imm_run(ctx, g.model, w.k, w.epsilon, w.ell, w.seed)
+
+    for _ in range(args.warmup):
+        seeds, st = step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    stats = []
+    for _ in range(args.steps):
+        flush.fill_(2.0)  # L2 flush between timed iterations, outside the events
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        seeds, st = step()
+        b.record(stream)
+        evs.append((a, b))
+        stats.append(st)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = dist.max(statistics.mean(ms))
+
+    # roofline of the dominant kernel: the samplers, timed by CUDA events on
+    # the launching stream inside the library, over the timed steps
+    ms_sample = sum(s.ms_sample for s in stats)
+    edges = sum(s.sample_edges for s in stats)
+    members = sum(s.sample_members for s in stats)
+    launches = sum(s.sample_launches for s in stats)
+    algo_bytes = 8.0 * edges + 16.0 * members
+    achieved = algo_bytes / (ms_sample / 1e3) / 1e9 if ms_sample > 0 else 0.0
+    peak, peak_kind = measured_peaks()
+    st = stats[-1]
+    gteps = (st.sample_edges / (st.ms_sample / 1e3)) / 1e9 if st.ms_sample > 0 else 0.0
+
+    e2e = None
+    if not args.no_e2e:
+        # public API from pinned host buffers: upload + run + seeds read back
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hrow, hsrc, hw = pin(g.row), pin(g.src), pin(g.weight)
+        h2d = hrow.nbytes + hsrc.nbytes + hw.nbytes
+        d2h = 4 * w.k + 8 * 2
+        ctx2 = imm.imm_create(device=dev, stream=stream)
+        tt = []
+        for it in range(args.warmup + args.steps):
+            flush.fill_(3.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            imm.imm_load_graph(ctx2, g.n, g.m, hrow, hsrc, hw, g.model)
+            s2, _ = imm.imm_run(ctx2, g.model, w.k, w.epsilon, w.ell, w.seed)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                tt.append(time.perf_counter() - t0)
+            assert np.array_equal(s2, seeds)
+        imm.imm_destroy(ctx2)
+        e2e = {"value": dist.max(statistics.mean(tt)), "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        rounds_sets = [st.sets_i[i] for i in range(st.rounds)] + [st.num_sets]
+        r = cpu_baseline(w, args.cpu_sample_seconds, st.num_sets, rounds_sets, w.k)
+        cpu = {"value": r["seconds"], "unit": "s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": ms_step / 1e3,
+            "unit": "s",
+            "n_gpus": dist.world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": w.desc, "graph": "R-MAT a=.57 b=.19 c=.19, transposed CSR",
+                       "l2": "256 MB buffer written between timed steps (outside the events)",
+                       "parallelism": f"replicas x{dist.world}"},
+            "sampling_gteps": gteps,
+            "sets_per_s": st.num_sets / (st.ms_sample / 1e3) if st.ms_sample > 0 else None,
+            "imm": {"theta": st.theta, "num_sets": st.num_sets, "members": st.members, "rounds": st.rounds,
+                    "lb": st.lb, "covered": st.covered, "ms_sample": st.ms_sample, "ms_index": st.ms_index,
+                    "ms_select": st.ms_select, "seeds_head": [int(x) for x in seeds[:10]]},
+            "roofline": {"kernel": "ic_small_kernel + ic_large_kernel (RRR sampling)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes": "8 B per examined in-edge + 16 B per member",
+                         "launches": launches},
+            "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    imm.imm_destroy(ctx)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_gpu(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

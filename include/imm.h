@@ -1,0 +1,194 @@
+/*
+ * imm.h — C ABI of the GB300 IMM hot path (EfficientIMM, arXiv 2411.09473).
+ *
+ * The library samples random reverse-reachable (RRR) sets on the GPU and runs
+ * greedy max-coverage seed selection over them, under the Independent Cascade
+ * (IC) and Linear Threshold (LT) models.  Every kernel is hand-written CUDA for
+ * sm_103a; this header is the only interface (plain C types, no torch types).
+ *
+ * Conventions shared by every call
+ *   - Return value: IMM_OK (0) or one of the IMM_E* codes below.  On error the
+ *     context stays usable; imm_last_error() describes the failure.
+ *   - Host pointers are caller-owned and only read (or written, for outputs)
+ *     during the call; the library never keeps them.
+ *   - Device memory is library-owned.  It comes from the optional allocator
+ *     given to imm_create (e.g. PyTorch's caching allocator), otherwise from
+ *     cudaMallocAsync on the context's stream.
+ *   - All GPU work of a context is issued on the stream given to imm_create
+ *     (NULL = the legacy default stream).  Calls that return host results
+ *     synchronise that stream before returning.
+ *   - Vertex ids are uint32 (n < 2^32 - 1); edge ids are uint32 positions in
+ *     the in-edge array (m < 2^32); set ids are uint64 but a stream holds fewer
+ *     than 2^32 - 1 sets (occurrence counts are uint32).
+ *   - Randomness: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ *     rng seed.  Root of set s: words 0,1 of Philox(ctr=(s_lo,s_hi,0,1));
+ *     IC coin of in-edge e: word e&3 of Philox(ctr=(s_lo,s_hi,e>>2,2));
+ *     LT draw at vertex v: word 0 of Philox(ctr=(s_lo,s_hi,v,3)).  Each set is
+ *     therefore a pure function of (graph, seed, set id), whatever the
+ *     traversal order, launch shape or batching.
+ *   - Not thread-safe: one host thread drives a context at a time.
+ */
+#ifndef IMM_H
+#define IMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define IMM_OK        0
+#define IMM_EINVAL    1  /* bad argument or malformed graph */
+#define IMM_ENOMEM    2  /* device allocation failed or arena limit reached */
+#define IMM_ECUDA     3  /* a CUDA runtime call or kernel failed */
+#define IMM_ETIMEOUT  4  /* a bounded device wait gave up */
+#define IMM_ESTATE    5  /* call not valid in the context's current state */
+
+/* ---- diffusion models (Sec. II-A) ---- */
+#define IMM_IC 0
+#define IMM_LT 1
+
+typedef struct imm_ctx imm_ctx;
+
+/* Optional device allocator.  alloc returns a device pointer of at least
+ * `bytes` bytes usable on `stream`, or NULL on failure; free releases it. */
+typedef struct imm_alloc {
+    void* (*alloc)(void* user, size_t bytes, void* stream);
+    void (*free)(void* user, void* ptr, size_t bytes, void* stream);
+    void* user;
+} imm_alloc;
+
+#define IMM_MAX_ROUNDS 64
+
+/* Statistics of one imm_run (all fields written by the call). */
+typedef struct imm_stats {
+    uint32_t rounds;                      /* sampling-phase rounds executed (Alg. 1 loop) */
+    uint32_t stopped_early;               /* 1 if the OPT lower-bound test fired */
+    uint64_t theta_i[IMM_MAX_ROUNDS];     /* theta_i of each round */
+    uint64_t covered_i[IMM_MAX_ROUNDS];   /* sets covered by that round's selection */
+    uint64_t sets_i[IMM_MAX_ROUNDS];      /* stream size at that round's selection */
+    double lb;                            /* lower bound on OPT (1 if the test never fired) */
+    uint64_t theta;                       /* Set_Theta result, ceil(lambda* / LB) */
+    uint64_t num_sets;                    /* final stream size, max(theta, sets so far) */
+    uint64_t covered;                     /* sets covered by the final seed set */
+    double lambda_prime;
+    double lambda_star;
+    uint64_t members;                     /* sum of set sizes over the final stream */
+    uint64_t edges_examined;              /* IC: in-edges whose coin was read; LT: walk steps */
+    double ms_total;                      /* host wall time of the call */
+    double ms_sample;                     /* device time of sampling kernels (CUDA events) */
+    double ms_select;                     /* device time of selection kernels (CUDA events) */
+    double ms_index;                      /* device time of compaction + inverted-index kernels */
+    uint64_t sample_launches;             /* sampler kernel launches (timed by ms_sample) */
+    uint64_t kernel_launches;             /* all kernel launches issued by the call */
+    uint64_t sample_edges;                /* same as edges_examined, for the timed launches */
+    uint64_t sample_members;              /* members produced by the timed sampler launches */
+} imm_stats;
+
+/* Create a context on CUDA device `device`.  `alloc` may be NULL (then
+ * cudaMallocAsync is used); `stream` is a cudaStream_t or NULL.
+ * Errors: EINVAL (out==NULL or bad device), ECUDA. */
+int imm_create(imm_ctx** out, int device, const imm_alloc* alloc, void* stream);
+
+/* Destroy a context and free all its device memory.  NULL is a no-op. */
+void imm_destroy(imm_ctx* ctx);
+
+/* Message describing the context's most recent error (owned by the context,
+ * valid until the next call on it).  Never NULL. */
+const char* imm_last_error(imm_ctx* ctx);
+
+/* Load a directed graph G = (V, E) (Sec. II-A) as CSR of its transpose, i.e.
+ * in-edges grouped by head v: in-edges of v are positions
+ * in_row[v] .. in_row[v+1]-1 of in_src (their tails u) and weight.
+ * weight[e] is p_uv for IMM_IC (edge live with that probability) or w_uv for
+ * IMM_LT (sum over a head's in-edges <= 1 + 1e-6).  Host pointers, copied in.
+ * The library derives per-edge integer thresholds on the device:
+ *   IC: thr[e] = ceilf(p_e * 2^24) (fp32, exact);
+ *   LT: cthr[e] = min(ceil(cw_e * 2^24), 2^24), cw_e the fp64 left-to-right
+ *       running sum of the head's weights in CSR order.
+ * Replaces any previous graph and drops the current RRR-set stream.
+ * Errors: EINVAL (n < 2, in_row[0] != 0, in_row[n] != m, in_row not
+ * monotone, in_src[e] >= n, weight NaN/<0/>1, LT head sum > 1 + 1e-6,
+ * m >= 2^32), ENOMEM, ECUDA. */
+int imm_load_graph(imm_ctx* ctx, uint32_t n, uint64_t m, const uint64_t* in_row,
+                   const uint32_t* in_src, const float* weight, int model);
+
+/* Same as imm_load_graph with DEVICE pointers (on the context's device,
+ * readable on its stream).  The data is copied into library memory. */
+int imm_load_graph_device(imm_ctx* ctx, uint32_t n, uint64_t m, const uint64_t* d_in_row,
+                          const uint32_t* d_in_src, const float* d_weight, int model);
+
+/* Generate_RRRsets (Alg. 1 lines 3 and 9; Alg. 3): extend the RRR-set stream
+ * to `theta` sets by sampling set ids |R| .. theta-1 with `rng_seed`
+ * (no-op if theta <= |R|).  Each set: a root drawn uniformly from V, then
+ *   IC: every vertex that reaches the root through live in-edges (reverse
+ *       probabilistic BFS; in-edge e live iff (coin >> 8) < thr[e]);
+ *   LT: the reverse walk that at vertex v picks the first in-edge j with
+ *       (draw >> 8) < cthr[j], stopping when none is picked or the picked
+ *       tail is already in the set.
+ * Members are stored contiguously per set in set-id order (prefix-sum
+ * compaction into the device arena) and counted into the per-vertex
+ * occurrence counter (Alg. 3, fused count).
+ * Errors: EINVAL (model differs from the loaded graph's, theta >= 2^32-1),
+ * ESTATE (no graph, or rng_seed differs from the current stream's: call
+ * imm_reset_sets first), ENOMEM (arena limit or allocation), ECUDA. */
+int imm_sample(imm_ctx* ctx, int model, uint64_t theta, uint64_t rng_seed);
+
+/* Find_Most_Influential_Set (Alg. 2): greedy max coverage over the current
+ * stream.  k rounds; each picks the vertex not yet picked with the most
+ * occurrences among uncovered sets (ties -> lowest id; picking continues at
+ * count 0), marks every uncovered set holding it covered and removes those
+ * sets' members from the counts (by decrement, or by recounting the
+ * uncovered sets when that is less work: Sec. IV-C adaptive counter update;
+ * the result is identical).  Writes the k picks in order to seeds_out (host,
+ * k entries) and the number of covered sets to *covered_out (host, nullable).
+ * Errors: EINVAL (k == 0, k > n, seeds_out NULL), ESTATE (no graph), ECUDA. */
+int imm_select(imm_ctx* ctx, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out);
+
+/* IMM (Alg. 1 with Tang, Shi & Xiao 2015's Theta_Estimation,
+ * OPT_Lower_Bound and Set_Theta): drops the current stream, then
+ *   ell' = ell (1 + ln2 / ln n), eps' = sqrt(2) eps,
+ *   for i = 1 .. ceil(log2 n) - 1: x = n / 2^i, sample to ceil(lambda'/x),
+ *     select k; stop with LB = nF/(1+eps') once nF = n*covered/|R| >= (1+eps') x;
+ *   theta = ceil(lambda* / LB); sample to max(theta, |R|); select k.
+ * lambda' and lambda* as in Tang et al.; host fp64, no FMA contraction.
+ * Writes k seeds to seeds_out (host) and, if stats_out != NULL, *stats_out.
+ * Errors: EINVAL (k == 0, k > n, eps not in (0,1), ell <= 0, model differs
+ * from the graph's, theta would reach 2^32-1), ESTATE, ENOMEM, ECUDA. */
+int imm_run(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell,
+            uint64_t rng_seed, uint32_t* seeds_out, imm_stats* stats_out);
+
+/* Drop the RRR-set stream (counts, arena, index); keeps the graph. */
+int imm_reset_sets(imm_ctx* ctx);
+
+/* Number of sets in the stream and total members (either pointer nullable). */
+int imm_stream_size(imm_ctx* ctx, uint64_t* num_sets, uint64_t* num_members);
+
+/* Test hook: members of stored set `set_id`, sorted ascending, into buf
+ * (host, cap entries); *len receives the set's size.
+ * Errors: EINVAL (set_id >= |R|, len NULL, or size > cap). */
+int imm_get_set(imm_ctx* ctx, uint64_t set_id, uint32_t* buf, uint32_t cap, uint32_t* len);
+
+/* Test hook: sets first .. first+count-1 in stored layout.  off_out (host,
+ * count+1 entries) receives offsets relative to the first set's start;
+ * mem_out (host, cap entries) receives the members (traversal order inside
+ * each set, not sorted).  off_out is filled even when the members do not
+ * fit, so a call with cap = 0 sizes the buffer.  Errors: EINVAL (range
+ * outside the stream, or members > cap). */
+int imm_get_sets(imm_ctx* ctx, uint64_t first, uint64_t count, uint64_t* off_out,
+                 uint32_t* mem_out, uint64_t cap);
+
+/* Test hook: per-vertex occurrence counts over the whole stream (host, n). */
+int imm_get_counts(imm_ctx* ctx, uint32_t* cnt_out);
+
+/* Limit on device bytes for the RRR-set arena and its inverted index
+ * (0 = unlimited).  imm_sample returns ENOMEM instead of growing past it. */
+int imm_set_arena_limit(imm_ctx* ctx, uint64_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMM_H */

@@ -1,0 +1,843 @@
+// Host runtime behind include/imm.h: context, device memory (pooled arena),
+// sampling batches, selection rounds and the IMM theta control.
+//
+// The theta control follows EfficientIMM Alg. 1 with the three steps it names
+// from Tang, Shi & Xiao (SIGMOD 2015): Theta_Estimation (lambda'), the
+// OPT_Lower_Bound test and Set_Theta (lambda*).  It runs in host fp64 with no
+// FMA contraction (-ffp-contract=off), so theta, LB and the ladder are
+// bit-identical to any other IEEE evaluation in the same order.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "imm.h"
+#include "imm_internal.cuh"
+
+using namespace imm;
+
+namespace {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Segment {
+    uint64_t set_begin = 0, set_end = 0;
+    DBuf voff;  // n+1 uint64
+    DBuf inv;   // members uint32
+};
+
+constexpr double kE = 2.71828182845904523536;  // the double nearest e
+
+}  // namespace
+
+struct imm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    imm_alloc alloc{};
+    bool has_alloc = false;
+    DeviceInfo di{};
+    std::string err = "no error";
+
+    // graph
+    bool loaded = false;
+    uint32_t n = 0;
+    uint64_t m = 0;
+    int model = IMM_IC;
+    DBuf row, src, thr;
+
+    // RRR-set stream
+    bool have_stream = false;
+    uint64_t seed = 0;
+    uint64_t nsets = 0;
+    uint64_t nmembers = 0;
+    DBuf off;   // uint64 [off_cap + 1]
+    uint64_t off_cap = 0;
+    DBuf arena;  // uint32 [arena_cap]
+    uint64_t arena_cap = 0;
+    DBuf cnt;  // uint32 [n]
+    std::vector<Segment> segs;
+    uint64_t index_bytes = 0;
+
+    // sampling scratch
+    DBuf set_len, set_pos, set_edges, large_q;
+    uint32_t batch_cap = 0;
+    DBuf stage;
+    uint64_t stage_cap = 0;
+    DBuf scalars;
+    DBuf scan_tmp;
+    DBuf slot_q, slot_bm;
+    uint32_t nslots = 0;
+    uint64_t slot_words = 0;
+    DBuf hist, cursor, vtmp;
+
+    // selection scratch
+    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, seeds, dsegs;
+
+    DBuf flags;
+    uint64_t arena_limit = 0;
+    uint32_t next_batch = 1u << 22;
+    double avg_len = 0.0;
+
+    // accounting for imm_stats
+    double acc_sample_ms = 0, acc_select_ms = 0, acc_index_ms = 0;
+    uint64_t acc_sample_launches = 0, acc_launches = 0, acc_edges = 0, acc_sample_members = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+int set_err(imm_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return code;
+}
+
+int cuda_err(imm_ctx* c, cudaError_t e, const char* where)
+{
+    return set_err(c, IMM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_err(c, e_, #call);     \
+    } while (0)
+
+#define TRY(call)                     \
+    do {                              \
+        int r_ = (call);              \
+        if (r_ != IMM_OK) return r_;  \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void dfree(imm_ctx* c, DBuf& b)
+{
+    if (b.p) {
+        if (c->has_alloc) c->alloc.free(c->alloc.user, b.p, b.bytes, c->stream);
+        else cudaFreeAsync(b.p, c->stream);
+    }
+    b = DBuf{};
+}
+
+int dalloc(imm_ctx* c, DBuf& b, size_t bytes)
+{
+    dfree(c, b);
+    if (bytes < 16) bytes = 16;
+    bytes = (bytes + 255) / 256 * 256;
+    void* p = nullptr;
+    if (c->has_alloc) {
+        p = c->alloc.alloc(c->alloc.user, bytes, c->stream);
+    } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) return set_err(c, IMM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    b.p = p;
+    b.bytes = bytes;
+    return IMM_OK;
+}
+
+// grow (contents discarded)
+int ensure(imm_ctx* c, DBuf& b, size_t bytes)
+{
+    if (b.bytes >= bytes) return IMM_OK;
+    size_t want = std::max(bytes, b.bytes + b.bytes / 2);
+    return dalloc(c, b, want);
+}
+
+// grow keeping the first `used` bytes
+int grow_keep(imm_ctx* c, DBuf& b, size_t need, size_t used)
+{
+    if (b.bytes >= need) return IMM_OK;
+    DBuf nb;
+    size_t want = std::max(need, b.bytes + b.bytes / 2);
+    if (dalloc(c, nb, want) != IMM_OK) {
+        if (dalloc(c, nb, need) != IMM_OK) return IMM_ENOMEM;
+    }
+    if (used) {
+        cudaError_t e = cudaMemcpyAsync(nb.p, b.p, used, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) {
+            dfree(c, nb);
+            return cuda_err(c, e, "arena copy");
+        }
+    }
+    dfree(c, b);
+    b = nb;
+    return IMM_OK;
+}
+
+template <typename T>
+T* P(const DBuf& b)
+{
+    return reinterpret_cast<T*>(b.p);
+}
+
+double elapsed(imm_ctx* c, int a, int b)
+{
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]);
+    return (double)ms;
+}
+
+void drop_stream(imm_ctx* c)
+{
+    for (auto& s : c->segs) {
+        dfree(c, s.voff);
+        dfree(c, s.inv);
+    }
+    c->segs.clear();
+    c->index_bytes = 0;
+    c->have_stream = false;
+    c->nsets = 0;
+    c->nmembers = 0;
+    c->avg_len = 0.0;
+    c->next_batch = 1u << 22;
+    if (c->off.p) cudaMemsetAsync(c->off.p, 0, sizeof(uint64_t), c->stream);
+    if (c->cnt.p) cudaMemsetAsync(c->cnt.p, 0, (size_t)c->n * 4, c->stream);
+}
+
+void free_graph(imm_ctx* c)
+{
+    drop_stream(c);
+    dfree(c, c->row);
+    dfree(c, c->src);
+    dfree(c, c->thr);
+    dfree(c, c->cnt);
+    dfree(c, c->hist);
+    dfree(c, c->cursor);
+    dfree(c, c->vtmp);
+    dfree(c, c->work);
+    dfree(c, c->picked);
+    dfree(c, c->slot_q);
+    dfree(c, c->slot_bm);
+    c->nslots = 0;
+    c->loaded = false;
+}
+
+DevGraph dev_graph(imm_ctx* c)
+{
+    DevGraph g;
+    g.n = c->n;
+    g.m = c->m;
+    g.row = P<uint64_t>(c->row);
+    g.src = P<uint32_t>(c->src);
+    g.thr = P<uint32_t>(c->thr);
+    return g;
+}
+
+uint64_t device_free_bytes()
+{
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return fr;
+}
+
+int load_graph_common(imm_ctx* c, uint32_t n, uint64_t m, const void* row, const void* src, const void* w,
+                      int model, cudaMemcpyKind kind)
+{
+    if (n < 2 || n == 0xFFFFFFFFu) return set_err(c, IMM_EINVAL, "n must be in [2, 2^32-2], got %u", n);
+    if (m >= 0xFFFFFFFFull) return set_err(c, IMM_EINVAL, "m must be < 2^32-1");
+    if (model != IMM_IC && model != IMM_LT) return set_err(c, IMM_EINVAL, "unknown model %d", model);
+    if (!row || (m && (!src || !w))) return set_err(c, IMM_EINVAL, "null graph array");
+    free_graph(c);
+    const uint64_t m_pad = std::max<uint64_t>((m + 3) & ~3ull, 4);
+    DBuf wbuf;
+    TRY(dalloc(c, c->row, ((size_t)n + 1) * 8));
+    TRY(dalloc(c, c->src, m_pad * 4));
+    TRY(dalloc(c, c->thr, m_pad * 4));
+    TRY(dalloc(c, wbuf, std::max<uint64_t>(m, 1) * 4));
+    TRY(ensure(c, c->flags, 64));
+    CK(cudaMemcpyAsync(c->row.p, row, ((size_t)n + 1) * 8, kind, c->stream));
+    CK(cudaMemsetAsync(c->src.p, 0, m_pad * 4, c->stream));
+    CK(cudaMemsetAsync(c->thr.p, 0, m_pad * 4, c->stream));
+    if (m) {
+        CK(cudaMemcpyAsync(c->src.p, src, m * 4, kind, c->stream));
+        CK(cudaMemcpyAsync(wbuf.p, w, m * 4, kind, c->stream));
+    }
+    CK(cudaMemsetAsync(c->flags.p, 0, 64, c->stream));
+    CK(launch_validate_graph(P<uint64_t>(c->row), P<uint32_t>(c->src), P<float>(wbuf), n, m, model,
+                             P<int>(c->flags), c->stream));
+    int flags = 0;
+    CK(cudaMemcpyAsync(&flags, c->flags.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (flags) {
+        dfree(c, wbuf);
+        free_graph(c);
+        return set_err(c, IMM_EINVAL, "malformed graph (flags 0x%x: 1=row offsets, 2=src >= n, 4=weight)",
+                       flags);
+    }
+    CK(launch_thresholds(P<uint64_t>(c->row), P<float>(wbuf), n, m, model, P<uint32_t>(c->thr),
+                         P<int>(c->flags), c->stream));
+    CK(cudaMemcpyAsync(&flags, c->flags.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, wbuf);
+    if (flags) {
+        free_graph(c);
+        return set_err(c, IMM_EINVAL, "LT in-weights of some head sum to more than 1 + 1e-6");
+    }
+    c->n = n;
+    c->m = m;
+    c->model = model;
+    TRY(dalloc(c, c->cnt, (size_t)n * 4));
+    CK(cudaMemsetAsync(c->cnt.p, 0, (size_t)n * 4, c->stream));
+    TRY(dalloc(c, c->off, 8 * 1024));
+    c->off_cap = 1023;
+    CK(cudaMemsetAsync(c->off.p, 0, 8, c->stream));
+    c->loaded = true;
+    return IMM_OK;
+}
+
+int ensure_slots(imm_ctx* c, uint32_t want_slots, bool need_bitmap)
+{
+    const uint64_t words = ((uint64_t)c->n + 31) / 32;
+    if (c->nslots >= want_slots && (!need_bitmap || c->slot_bm.bytes >= (size_t)want_slots * words * 4))
+        return IMM_OK;
+    TRY(dalloc(c, c->slot_q, (size_t)want_slots * c->n * 4));
+    if (need_bitmap) {
+        TRY(dalloc(c, c->slot_bm, (size_t)want_slots * words * 4));
+        CK(cudaMemsetAsync(c->slot_bm.p, 0, (size_t)want_slots * words * 4, c->stream));
+    }
+    c->nslots = want_slots;
+    c->slot_words = words;
+    return IMM_OK;
+}
+
+int index_limit_ok(imm_ctx* c, uint64_t more_bytes)
+{
+    if (!c->arena_limit) return IMM_OK;
+    const uint64_t used = c->arena_cap * 4 + c->index_bytes;
+    if (used + more_bytes > c->arena_limit)
+        return set_err(c, IMM_ENOMEM, "arena limit of %llu bytes reached", (unsigned long long)c->arena_limit);
+    return IMM_OK;
+}
+
+// Rebuild the inverted index as a single segment over the whole stream.
+int merge_segments(imm_ctx* c)
+{
+    for (auto& s : c->segs) {
+        dfree(c, s.voff);
+        dfree(c, s.inv);
+    }
+    c->segs.clear();
+    c->index_bytes = 0;
+    Segment seg;
+    seg.set_begin = 0;
+    seg.set_end = c->nsets;
+    TRY(dalloc(c, seg.voff, ((size_t)c->n + 1) * 8));
+    TRY(dalloc(c, seg.inv, std::max<uint64_t>(c->nmembers, 1) * 4));
+    CK(launch_vertex_scan(P<uint32_t>(c->cnt), c->n, P<uint64_t>(seg.voff), nullptr, P<uint32_t>(c->cursor),
+                          P<uint64_t>(c->vtmp), c->di, c->stream));
+    CK(launch_index_scatter(0, c->nsets, P<uint64_t>(c->off), P<uint32_t>(c->arena), P<uint64_t>(seg.voff),
+                            P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di, c->stream));
+    c->acc_launches += 4;
+    c->index_bytes = seg.voff.bytes + seg.inv.bytes;
+    c->segs.push_back(seg);
+    return IMM_OK;
+}
+
+// Generate_RRRsets: extend the stream to theta sets.
+int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
+{
+    if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
+    if (theta >= 0xFFFFFFFFull) return set_err(c, IMM_EINVAL, "theta must be < 2^32-1");
+    if (c->have_stream && c->nsets > 0 && c->seed != seed)
+        return set_err(c, IMM_ESTATE, "rng seed differs from the current stream's; reset first");
+    c->have_stream = true;
+    c->seed = seed;
+    const DevGraph g = dev_graph(c);
+    const bool ic = c->model == IMM_IC;
+    const uint64_t words = ((uint64_t)c->n + 31) / 32;
+    TRY(ensure(c, c->scalars, sizeof(BatchScalars)));
+    TRY(ensure(c, c->hist, (size_t)c->n * 4));
+    TRY(ensure(c, c->cursor, (size_t)c->n * 4));
+    TRY(ensure(c, c->vtmp, scan_tmp_words(c->n) * 8));
+
+    while (c->nsets < theta) {
+        const uint64_t want = theta - c->nsets;
+        // Staging holds the members of one batch.  Its size follows the mean
+        // set size seen so far (at least one whole-graph set, at most 1.5e9
+        // members or an eighth of free memory); the batch takes as many sets
+        // as are expected to fit with 30% headroom.
+        const double avg = c->avg_len > 0 ? c->avg_len : 64.0;
+        {
+            const uint64_t floor_cap = (uint64_t)c->n + 4096;
+            const uint64_t fr = device_free_bytes() + c->stage.bytes;
+            const uint64_t stage_max = std::max<uint64_t>(floor_cap, std::min<uint64_t>(1500000000ull, fr / 8 / 4));
+            const double ideal = avg * 1.3 * (double)std::min<uint64_t>(want, c->next_batch);
+            const uint64_t need = std::max<uint64_t>(floor_cap, (uint64_t)std::min(ideal, (double)stage_max));
+            if (c->stage_cap < need) {
+                TRY(dalloc(c, c->stage, need * 4));
+                c->stage_cap = need;
+            }
+        }
+        uint64_t fit = (uint64_t)((double)c->stage_cap / (avg * 1.3));
+        uint32_t count = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(want, c->next_batch), std::max<uint64_t>(fit, 1));
+        if (count == 0) count = 1;
+        // batch buffers
+        if (c->batch_cap < count) {
+            const uint32_t cap = std::max(count, c->batch_cap + c->batch_cap / 2);
+            TRY(dalloc(c, c->set_len, (size_t)cap * 4));
+            TRY(dalloc(c, c->set_pos, (size_t)cap * 8));
+            TRY(dalloc(c, c->set_edges, (size_t)cap * 4));
+            TRY(dalloc(c, c->large_q, (size_t)cap * 4));
+            TRY(dalloc(c, c->scan_tmp, scan_tmp_words(cap) * 8));
+            c->batch_cap = cap;
+        }
+        // arena offsets: room for base + count + 1 entries
+        if (c->off_cap < c->nsets + count) {
+            const uint64_t need = c->nsets + count;
+            const uint64_t cap = std::max(need, c->off_cap + c->off_cap / 2);
+            TRY(grow_keep(c, c->off, (cap + 1) * 8, (c->nsets + 1) * 8));
+            c->off_cap = cap;
+        }
+
+        BatchScalars* sc = P<BatchScalars>(c->scalars);
+        CK(cudaMemsetAsync(sc, 0, sizeof(BatchScalars), c->stream));
+        CK(cudaMemsetAsync(&sc->first_fail, 0xFF, 4, c->stream));
+        SampleBatch b;
+        b.seed = seed;
+        b.base = c->nsets;
+        b.count = count;
+        b.set_len = P<uint32_t>(c->set_len);
+        b.set_pos = P<uint64_t>(c->set_pos);
+        b.set_edges = P<uint32_t>(c->set_edges);
+        b.stage = P<uint32_t>(c->stage);
+        b.stage_cap = c->stage_cap;
+        b.large_q = P<uint32_t>(c->large_q);
+        b.sc = sc;
+
+        CK(cudaEventRecord(c->ev[0], c->stream));
+        if (ic) CK(launch_ic_small(g, b, c->di, c->stream));
+        else CK(launch_lt_small(g, b, c->di, c->stream));
+        CK(cudaEventRecord(c->ev[1], c->stream));
+        uint32_t large_count = 0;
+        CK(cudaMemcpyAsync(&large_count, &sc->large_count, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->acc_sample_ms += elapsed(c, 0, 1);
+        c->acc_sample_launches += 1;
+        c->acc_launches += 1;
+        if (large_count) {
+            LargeSlots ls;
+            if (ic) {
+                const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
+                TRY(ensure_slots(c, (uint32_t)c->di.sms, !smem));
+            } else {
+                TRY(ensure_slots(c, (uint32_t)std::min(c->di.sms * 2, 1024), true));
+            }
+            ls.queues = P<uint32_t>(c->slot_q);
+            ls.queue_cap = c->n;
+            ls.bitmaps = P<uint32_t>(c->slot_bm);
+            ls.bitmap_words = words;
+            ls.nslots = std::min<uint32_t>(c->nslots, large_count);
+            CK(cudaEventRecord(c->ev[0], c->stream));
+            if (ic) CK(launch_ic_large(g, b, ls, c->di, c->stream));
+            else CK(launch_lt_long(g, b, ls, c->di, c->stream));
+            CK(cudaEventRecord(c->ev[1], c->stream));
+            c->acc_sample_launches += 1;
+            c->acc_launches += 1;
+        }
+        CK(cudaEventRecord(c->ev[2], c->stream));
+        CK(launch_batch_scan(b, P<uint64_t>(c->off), P<uint64_t>(c->scan_tmp), c->di, c->stream));
+        c->acc_launches += 3;
+        BatchScalars hs;
+        CK(cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (large_count) c->acc_sample_ms += elapsed(c, 0, 1);
+        if (hs.error) return set_err(c, IMM_ECUDA, "sampler reported device error 0x%x", hs.error);
+        const uint64_t committed = hs.committed;
+        const uint64_t bm = hs.members;
+        if (committed == 0) {
+            if (count == 1) return set_err(c, IMM_ENOMEM, "staging buffer cannot hold one RRR set");
+            c->next_batch = std::max<uint32_t>(1, count / 4);
+            c->avg_len = std::max(c->avg_len * 2.0, (double)hs.stage_cursor / (double)count);
+            continue;
+        }
+        // arena + this segment's index
+        const uint64_t seg_bytes = ((uint64_t)c->n + 1) * 8 + bm * 4;
+        if (c->arena_cap < c->nmembers + bm) {
+            const uint64_t need = c->nmembers + bm;
+            uint64_t cap = std::max(need, c->arena_cap + c->arena_cap / 2);
+            if (c->arena_limit && (cap * 4 + c->index_bytes + seg_bytes > c->arena_limit)) cap = need;
+            TRY(index_limit_ok(c, (cap - c->arena_cap) * 4 + seg_bytes));
+            TRY(grow_keep(c, c->arena, cap * 4, c->nmembers * 4));
+            c->arena_cap = cap;
+        } else {
+            TRY(index_limit_ok(c, seg_bytes));
+        }
+        Segment seg;
+        seg.set_begin = c->nsets;
+        seg.set_end = c->nsets + committed;
+        TRY(dalloc(c, seg.voff, ((size_t)c->n + 1) * 8));
+        if (dalloc(c, seg.inv, std::max<uint64_t>(bm, 1) * 4) != IMM_OK) {
+            dfree(c, seg.voff);
+            return IMM_ENOMEM;
+        }
+        CK(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n * 4, c->stream));
+        CK(launch_compact(b, committed, P<uint64_t>(c->off), P<uint32_t>(c->arena), P<uint32_t>(c->hist), c->di,
+                          c->stream));
+        CK(launch_vertex_scan(P<uint32_t>(c->hist), c->n, P<uint64_t>(seg.voff), P<uint32_t>(c->cnt),
+                              P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di, c->stream));
+        CK(launch_index_scatter(seg.set_begin, seg.set_end, P<uint64_t>(c->off), P<uint32_t>(c->arena),
+                                P<uint64_t>(seg.voff), P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di,
+                                c->stream));
+        CK(cudaEventRecord(c->ev[3], c->stream));
+        c->acc_launches += 5;
+        c->index_bytes += seg.voff.bytes + seg.inv.bytes;
+        c->segs.push_back(seg);
+        c->nsets += committed;
+        c->nmembers += bm;
+        c->acc_edges += hs.edges;
+        c->acc_sample_members += bm;
+        CK(cudaEventSynchronize(c->ev[3]));
+        c->acc_index_ms += elapsed(c, 2, 3);
+        // running mean set size (drives the next batch's staging)
+        const double len = (double)bm / (double)committed;
+        c->avg_len = c->avg_len > 0 ? 0.5 * (c->avg_len + len) : len;
+        c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : (1u << 22);
+        if (c->segs.size() > 48) TRY(merge_segments(c));
+    }
+    return IMM_OK;
+}
+
+int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
+{
+    if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
+    if (k == 0 || k > c->n) return set_err(c, IMM_EINVAL, "k must be in [1, n]");
+    if (!seeds_out) return set_err(c, IMM_EINVAL, "seeds_out is NULL");
+    const uint64_t R = c->nsets;
+    TRY(ensure(c, c->work, (size_t)c->n * 4));
+    TRY(ensure(c, c->picked, (size_t)c->n));
+    TRY(ensure(c, c->covered, std::max<uint64_t>(R, 1)));
+    TRY(ensure(c, c->newly, std::max<uint64_t>(R, 1) * 4));
+    TRY(ensure(c, c->keys, (size_t)k * 8));
+    TRY(ensure(c, c->newly_n, (size_t)k * 8));
+    TRY(ensure(c, c->vol_cov, (size_t)k * 8));
+    TRY(ensure(c, c->seeds, (size_t)k * 4));
+    std::vector<DevSegment> hsegs;
+    for (auto& s : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(s.voff), P<uint32_t>(s.inv)});
+    TRY(ensure(c, c->dsegs, std::max<size_t>(hsegs.size(), 1) * sizeof(DevSegment)));
+
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    if (!hsegs.empty())
+        CK(cudaMemcpyAsync(c->dsegs.p, hsegs.data(), hsegs.size() * sizeof(DevSegment), cudaMemcpyHostToDevice,
+                           c->stream));
+    CK(cudaMemcpyAsync(c->work.p, c->cnt.p, (size_t)c->n * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(c->picked.p, 0, (size_t)c->n, c->stream));
+    if (R) CK(cudaMemsetAsync(c->covered.p, 0, R, c->stream));
+    CK(cudaMemsetAsync(c->keys.p, 0, (size_t)k * 8, c->stream));
+    CK(cudaMemsetAsync(c->newly_n.p, 0, (size_t)k * 8, c->stream));
+    CK(cudaMemsetAsync(c->vol_cov.p, 0, (size_t)k * 8, c->stream));
+
+    SelectState s;
+    s.n = c->n;
+    s.nsets = R;
+    s.total_members = c->nmembers;
+    s.off = P<uint64_t>(c->off);
+    s.arena = P<uint32_t>(c->arena);
+    s.work = P<uint32_t>(c->work);
+    s.picked = P<uint8_t>(c->picked);
+    s.covered = P<uint8_t>(c->covered);
+    s.newly = P<uint32_t>(c->newly);
+    s.keys = P<unsigned long long>(c->keys);
+    s.newly_n = P<unsigned long long>(c->newly_n);
+    s.vol_cov = P<unsigned long long>(c->vol_cov);
+    s.seeds = P<uint32_t>(c->seeds);
+    s.segs = P<DevSegment>(c->dsegs);
+    s.nsegs = (uint32_t)hsegs.size();
+    for (uint32_t j = 0; j < k; ++j) CK(launch_select_round(s, j, c->di, c->stream, &c->acc_launches));
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    std::vector<unsigned long long> nn(k);
+    CK(cudaMemcpyAsync(seeds_out, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(nn.data(), c->newly_n.p, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->acc_select_ms += elapsed(c, 0, 1);
+    uint64_t cov = 0;
+    for (uint32_t j = 0; j < k; ++j) cov += nn[j];
+    if (covered_out) *covered_out = cov;
+    return IMM_OK;
+}
+
+void reset_acc(imm_ctx* c)
+{
+    c->acc_sample_ms = c->acc_select_ms = c->acc_index_ms = 0;
+    c->acc_sample_launches = c->acc_launches = c->acc_edges = c->acc_sample_members = 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int imm_create(imm_ctx** out, int device, const imm_alloc* alloc, void* stream)
+{
+    if (!out) return IMM_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return IMM_EINVAL;
+    }
+    imm_ctx* c = new imm_ctx();
+    c->device = device;
+    DeviceGuard guard(device);
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return IMM_ECUDA;
+    }
+    c->di.sms = prop.multiProcessorCount;
+    c->di.max_smem_optin = (int)prop.sharedMemPerBlockOptin;
+    for (auto& e : c->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            delete c;
+            return IMM_ECUDA;
+        }
+    }
+    *out = c;
+    return IMM_OK;
+}
+
+void imm_destroy(imm_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    free_graph(c);
+    DBuf* bufs[] = {&c->off,     &c->arena,   &c->set_len, &c->set_pos, &c->set_edges, &c->large_q,
+                    &c->stage,   &c->scalars, &c->scan_tmp, &c->covered, &c->newly,    &c->keys,
+                    &c->newly_n, &c->vol_cov, &c->seeds,    &c->dsegs,   &c->flags};
+    for (DBuf* b : bufs) dfree(c, *b);
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+const char* imm_last_error(imm_ctx* c)
+{
+    return c ? c->err.c_str() : "null context";
+}
+
+int imm_load_graph(imm_ctx* c, uint32_t n, uint64_t m, const uint64_t* in_row, const uint32_t* in_src,
+                   const float* weight, int model)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    return load_graph_common(c, n, m, in_row, in_src, weight, model, cudaMemcpyHostToDevice);
+}
+
+int imm_load_graph_device(imm_ctx* c, uint32_t n, uint64_t m, const uint64_t* d_in_row, const uint32_t* d_in_src,
+                          const float* d_weight, int model)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    return load_graph_common(c, n, m, d_in_row, d_in_src, d_weight, model, cudaMemcpyDeviceToDevice);
+}
+
+int imm_sample(imm_ctx* c, int model, uint64_t theta, uint64_t rng_seed)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
+    if (model != c->model) return set_err(c, IMM_EINVAL, "model %d differs from the loaded graph's", model);
+    return sample_to(c, theta, rng_seed);
+}
+
+int imm_select(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    return select_k(c, k, seeds_out, covered_out);
+}
+
+int imm_reset_sets(imm_ctx* c)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    drop_stream(c);
+    return IMM_OK;
+}
+
+int imm_stream_size(imm_ctx* c, uint64_t* num_sets, uint64_t* num_members)
+{
+    if (!c) return IMM_EINVAL;
+    if (num_sets) *num_sets = c->nsets;
+    if (num_members) *num_members = c->nmembers;
+    return IMM_OK;
+}
+
+int imm_set_arena_limit(imm_ctx* c, uint64_t bytes)
+{
+    if (!c) return IMM_EINVAL;
+    c->arena_limit = bytes;
+    return IMM_OK;
+}
+
+int imm_run(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint64_t rng_seed, uint32_t* seeds_out,
+            imm_stats* stats_out)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
+    if (model != c->model) return set_err(c, IMM_EINVAL, "model %d differs from the loaded graph's", model);
+    if (k == 0 || k > c->n) return set_err(c, IMM_EINVAL, "k must be in [1, n]");
+    if (!(epsilon > 0.0 && epsilon < 1.0)) return set_err(c, IMM_EINVAL, "epsilon must be in (0, 1)");
+    if (!(ell > 0.0)) return set_err(c, IMM_EINVAL, "ell must be > 0");
+    if (!seeds_out) return set_err(c, IMM_EINVAL, "seeds_out is NULL");
+    drop_stream(c);
+    reset_acc(c);
+    imm_stats st;
+    std::memset(&st, 0, sizeof(st));
+
+    // Theta_Estimation constants (Tang et al.), same operation order as any
+    // plain fp64 evaluation of the formulas.
+    const double nd = (double)c->n;
+    const double ln_n = std::log(nd);
+    const double ell_p = ell * (1.0 + std::log(2.0) / ln_n);
+    const double eps_p = std::sqrt(2.0) * epsilon;
+    double lnC = 0.0;
+    for (uint32_t i = 1; i <= k; i++) lnC += std::log((double)(c->n - k + i)) - std::log((double)i);
+    const double lam_p =
+        (2.0 + 2.0 * eps_p / 3.0) * (lnC + ell_p * ln_n + std::log(std::log2(nd))) * nd / (eps_p * eps_p);
+    const double g = 1.0 - 1.0 / kE;
+    const double alpha = std::sqrt(ell_p * ln_n + std::log(2.0));
+    const double beta = std::sqrt(g * (lnC + ell_p * ln_n + std::log(2.0)));
+    const double t = g * alpha + beta;
+    const double lam_s = 2.0 * nd * t * t / (epsilon * epsilon);
+    uint32_t lg = 0;
+    while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)c->n) lg++;
+    const uint32_t rounds = lg >= 1 ? lg - 1 : 0;
+    st.lambda_prime = lam_p;
+    st.lambda_star = lam_s;
+
+    double lb = 1.0;
+    for (uint32_t i = 1; i <= rounds; i++) {
+        const double x = std::ldexp(nd, -(int)i);
+        const double th = std::ceil(lam_p / x);
+        if (th >= 4294967295.0) return set_err(c, IMM_EINVAL, "theta_%u exceeds 2^32-2", i);
+        const uint64_t theta_i = (uint64_t)th;
+        TRY(sample_to(c, theta_i, rng_seed));
+        uint64_t cov = 0;
+        TRY(select_k(c, k, seeds_out, &cov));
+        const double nF = nd * (double)cov / (double)c->nsets;
+        if (i - 1 < IMM_MAX_ROUNDS) {
+            st.theta_i[i - 1] = theta_i;
+            st.covered_i[i - 1] = cov;
+            st.sets_i[i - 1] = c->nsets;
+        }
+        st.rounds = i;
+        if (nF >= (1.0 + eps_p) * x) {
+            lb = nF / (1.0 + eps_p);
+            st.stopped_early = 1;
+            break;
+        }
+    }
+    const double tf = std::ceil(lam_s / lb);
+    if (tf >= 4294967295.0) return set_err(c, IMM_EINVAL, "theta exceeds 2^32-2");
+    const uint64_t theta = (uint64_t)tf;
+    st.lb = lb;
+    st.theta = theta;
+    TRY(sample_to(c, std::max<uint64_t>(theta, c->nsets), rng_seed));
+    uint64_t cov = 0;
+    TRY(select_k(c, k, seeds_out, &cov));
+    st.num_sets = c->nsets;
+    st.covered = cov;
+    st.members = c->nmembers;
+    st.edges_examined = c->acc_edges;
+    st.ms_sample = c->acc_sample_ms;
+    st.ms_select = c->acc_select_ms;
+    st.ms_index = c->acc_index_ms;
+    st.sample_launches = c->acc_sample_launches;
+    st.kernel_launches = c->acc_launches;
+    st.sample_edges = c->acc_edges;
+    st.sample_members = c->acc_sample_members;
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (stats_out) *stats_out = st;
+    return IMM_OK;
+}
+
+int imm_get_set(imm_ctx* c, uint64_t set_id, uint32_t* buf, uint32_t cap, uint32_t* len)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    if (set_id >= c->nsets || !len) return set_err(c, IMM_EINVAL, "set id out of range");
+    uint64_t o[2];
+    CK(cudaMemcpyAsync(o, P<uint64_t>(c->off) + set_id, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const uint64_t L = o[1] - o[0];
+    *len = (uint32_t)L;
+    if (L > cap || (L && !buf)) return set_err(c, IMM_EINVAL, "set has %llu members, cap %u", (unsigned long long)L, cap);
+    if (L) {
+        CK(cudaMemcpyAsync(buf, P<uint32_t>(c->arena) + o[0], L * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::sort(buf, buf + L);
+    }
+    return IMM_OK;
+}
+
+int imm_get_sets(imm_ctx* c, uint64_t first, uint64_t count, uint64_t* off_out, uint32_t* mem_out, uint64_t cap)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    if (first > c->nsets || count > c->nsets - first || !off_out) return set_err(c, IMM_EINVAL, "range outside the stream");
+    CK(cudaMemcpyAsync(off_out, P<uint64_t>(c->off) + first, (count + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const uint64_t a = off_out[0], b = off_out[count];
+    for (uint64_t i = 0; i <= count; ++i) off_out[i] -= a;
+    if (b - a > cap || (b > a && !mem_out)) return set_err(c, IMM_EINVAL, "range holds %llu members, cap %llu",
+                                                          (unsigned long long)(b - a), (unsigned long long)cap);
+    if (b > a) {
+        CK(cudaMemcpyAsync(mem_out, P<uint32_t>(c->arena) + a, (b - a) * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return IMM_OK;
+}
+
+int imm_get_counts(imm_ctx* c, uint32_t* cnt_out)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
+    if (!cnt_out) return set_err(c, IMM_EINVAL, "cnt_out is NULL");
+    CK(cudaMemcpyAsync(cnt_out, c->cnt.p, (size_t)c->n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IMM_OK;
+}
+
+}  // extern "C"

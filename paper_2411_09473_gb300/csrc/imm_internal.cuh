@@ -1,0 +1,170 @@
+// Internal declarations shared by the CUDA translation units of the IMM
+// library (device structs, the Philox device function, launch wrappers).
+// Not part of the public ABI (include/imm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace imm {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kLenPending = 0xFFFFFFFEu;  // set handed to the block / long-walk path
+constexpr uint32_t kLenFailed = 0xFFFFFFFFu;   // staging reservation failed; resample later
+constexpr uint32_t kTagRoot = 1, kTagIC = 2, kTagLT = 3;
+constexpr uint32_t kQ24 = 1u << 24;
+
+// Device error bits (written to BatchScalars::error).
+constexpr int kErrHashProbe = 1;
+constexpr int kErrQueue = 2;
+constexpr int kErrBadGraph = 4;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// -> 64-bit products whose halves are xored with the other counter words and
+// the round key; the key advances by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint2 philox_key(uint64_t seed)
+{
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Root of set s: uniform over [0, n) by multiply-shift of a 64-bit draw.
+__device__ __forceinline__ uint32_t draw_root(uint64_t seed, uint64_t s, uint32_t n)
+{
+    const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), 0u, kTagRoot), philox_key(seed));
+    const uint64_t x = ((uint64_t)w.y << 32) | w.x;
+    return (uint32_t)__umul64hi(x, (uint64_t)n);
+}
+
+// ---------------------------------------------------------------------------
+// Device-side views.
+// ---------------------------------------------------------------------------
+struct DevGraph {
+    uint32_t n;
+    uint64_t m;
+    const uint64_t* row;  // n+1 in-edge offsets (CSR of G^T)
+    const uint32_t* src;  // m (padded to a multiple of 4): tail of each in-edge
+    const uint32_t* thr;  // m (padded, zeros): IC threshold or LT cumulative threshold
+};
+
+// Counters and flags of one sampling batch (device memory, zeroed per batch
+// except first_fail, set to kEmpty).
+struct BatchScalars {
+    uint32_t cursor;        // next batch-relative set id for the small-set path
+    uint32_t large_count;   // sets handed to the large-set path
+    uint32_t large_cursor;  // next entry of the large-set queue
+    uint32_t first_fail;    // lowest batch-relative id whose staging reservation failed
+    unsigned long long stage_cursor;
+    unsigned long long edges;      // IC: in-edges whose coin was read; LT: walk steps
+    unsigned long long committed;  // sets kept (min(first_fail, count)), by the scan
+    unsigned long long members;    // members of the kept sets, by the scan
+    int error;
+    int pad;
+};
+
+struct SampleBatch {
+    uint64_t seed;
+    uint64_t base;      // first set id of the batch
+    uint32_t count;     // sets in the batch
+    uint32_t* set_len;  // [count]
+    uint64_t* set_pos;  // [count] staging offset
+    uint32_t* set_edges;  // [count] IC: in-edges of the members; LT: walk steps
+    uint32_t* stage;    // staging members
+    uint64_t stage_cap;
+    uint32_t* large_q;  // [count] batch-relative ids for the large-set path
+    BatchScalars* sc;
+};
+
+// Per-CTA scratch of the large-set path: a member queue of n entries and,
+// when the visited bitmap does not fit in shared memory, an n-bit bitmap.
+struct LargeSlots {
+    uint32_t* queues;
+    uint64_t queue_cap;
+    uint32_t* bitmaps;
+    uint64_t bitmap_words;
+    uint32_t nslots;
+};
+
+// One segment of the inverted index: sets [set_begin, set_end) whose
+// members were scattered by vertex: inv[voff[v] .. voff[v+1]) = ids of the
+// segment's sets that contain v.
+struct DevSegment {
+    const uint64_t* voff;
+    const uint32_t* inv;
+};
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (defined in the .cu files).
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+    int sms;
+    int max_smem_optin;
+};
+
+// graph
+cudaError_t launch_validate_graph(const uint64_t* row, const uint32_t* src, const float* w, uint32_t n,
+                                  uint64_t m, int model, int* d_flags, cudaStream_t st);
+cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, uint64_t m, int model,
+                              uint32_t* thr, int* d_flags, cudaStream_t st);
+
+// sampling
+int ic_large_uses_smem(uint32_t n, const DeviceInfo& di);
+cudaError_t launch_ic_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
+                            const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
+                           const DeviceInfo& di, cudaStream_t st);
+// exclusive scan of the kept sets' lengths into off[base+1 ..]; needs tmp of
+// scan_tmp_words(count) uint64
+uint64_t scan_tmp_words(uint32_t count);
+cudaError_t launch_batch_scan(const SampleBatch& b, uint64_t* off, uint64_t* tmp, const DeviceInfo& di,
+                              cudaStream_t st);
+cudaError_t launch_compact(const SampleBatch& b, uint64_t committed, const uint64_t* off, uint32_t* arena,
+                           uint32_t* seg_hist, const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff, uint32_t* cnt,
+                               uint32_t* cursor, uint64_t* tmp, const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_index_scatter(uint64_t set_begin, uint64_t set_end, const uint64_t* off,
+                                 const uint32_t* arena, const uint64_t* voff, uint32_t* cursor,
+                                 uint32_t* inv, const DeviceInfo& di, cudaStream_t st);
+
+// selection
+struct SelectState {
+    uint32_t n;
+    uint64_t nsets;
+    uint64_t total_members;
+    const uint64_t* off;
+    const uint32_t* arena;
+    uint32_t* work;      // n mutable counts
+    uint8_t* picked;     // n
+    uint8_t* covered;    // nsets
+    uint32_t* newly;     // nsets: ids covered in the current round
+    unsigned long long* keys;      // k: packed (count, ~v) argmax per round
+    unsigned long long* newly_n;   // k: sets covered per round
+    unsigned long long* vol_cov;   // k: members of the sets covered per round
+    uint32_t* seeds;     // k
+    const DevSegment* segs;
+    uint32_t nsegs;
+};
+cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
+                                uint64_t* launches);
+
+}  // namespace imm

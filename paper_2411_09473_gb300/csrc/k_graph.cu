@@ -1,0 +1,86 @@
+// Graph load kernels: CSR validation and per-edge integer thresholds.
+//
+// IC (Sec. II-A): in-edge e is live with probability p_e.  The coin compares
+// a 24-bit draw with thr[e] = ceilf(p_e * 2^24); the product by a power of two
+// is exact in fp32, so thr/2^24 is p_e rounded up to the 24-bit grid.
+// LT (Sec. II-A): a head keeps at most one in-edge, edge j with probability
+// w_j.  cthr[j] = min(ceil(cw_j * 2^24), 2^24) where cw_j is the fp64 running
+// sum of the head's fp32 weights in CSR order; the first j with draw < cthr[j]
+// is the kept edge.
+#include "imm_internal.cuh"
+
+namespace imm {
+
+constexpr int kFlagRow = 1;      // row not monotone / row[0] != 0 / row[n] != m
+constexpr int kFlagSrc = 2;      // src >= n
+constexpr int kFlagWeight = 4;   // NaN, < 0 or > 1
+constexpr int kFlagLtSum = 8;    // LT head sum > 1 + 1e-6
+
+__global__ void validate_rows_kernel(const uint64_t* row, uint32_t n, uint64_t m, int* flags)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (row[v + 1] < row[v]) atomicOr(flags, kFlagRow);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (row[0] != 0 || row[n] != m) atomicOr(flags, kFlagRow);
+    }
+}
+
+__global__ void validate_edges_kernel(const uint32_t* src, const float* w, uint32_t n, uint64_t m, int* flags)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    int f = 0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        if (src[e] >= n) f |= kFlagSrc;
+        const float x = w[e];
+        if (!(x >= 0.0f && x <= 1.0f)) f |= kFlagWeight;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+cudaError_t launch_validate_graph(const uint64_t* row, const uint32_t* src, const float* w, uint32_t n,
+                                  uint64_t m, int model, int* d_flags, cudaStream_t st)
+{
+    (void)model;
+    validate_rows_kernel<<<1024, 256, 0, st>>>(row, n, m, d_flags);
+    if (m) validate_edges_kernel<<<2048, 256, 0, st>>>(src, w, n, m, d_flags);
+    return cudaGetLastError();
+}
+
+__global__ void ic_threshold_kernel(const float* w, uint64_t m, uint32_t* thr)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        thr[e] = (uint32_t)ceilf(__fmul_rn(w[e], 16777216.0f));
+    }
+}
+
+// One thread per head: the running sum is sequential by definition.
+__global__ void lt_threshold_kernel(const uint64_t* row, const float* w, uint32_t n, uint32_t* cthr, int* flags)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        double cw = 0.0;
+        const uint64_t lo = row[v], hi = row[v + 1];
+        for (uint64_t e = lo; e < hi; ++e) {
+            cw = __dadd_rn(cw, (double)w[e]);
+            const double t = ceil(__dmul_rn(cw, 16777216.0));
+            cthr[e] = t > 16777216.0 ? kQ24 : (uint32_t)t;
+        }
+        if (cw > 1.0 + 1e-6) atomicOr(flags, kFlagLtSum);
+    }
+}
+
+cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, uint64_t m, int model,
+                              uint32_t* thr, int* d_flags, cudaStream_t st)
+{
+    if (model == 0) {
+        if (m) ic_threshold_kernel<<<2048, 256, 0, st>>>(w, m, thr);
+    } else {
+        lt_threshold_kernel<<<(n + 255) / 256, 256, 0, st>>>(row, w, n, thr, d_flags);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace imm

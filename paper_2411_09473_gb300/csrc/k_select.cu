@@ -1,0 +1,225 @@
+// Greedy max-coverage seed selection (Find_Most_Influential_Set, EfficientIMM
+// Alg. 2) over the RRR-set stream.  One round = five launches on the stream:
+//
+//   argmax        PARALLEL_REDUCTION (Sec. IV-A): max over vertices not yet
+//                 picked of key = (count << 32) | (2^32 - 1 - v), so ties go to
+//                 the lowest id; thread -> warp shuffle -> block -> atomicMax.
+//   cover         every set holding the pick (read from the inverted index
+//                 segments) that is not yet covered is marked covered and
+//                 appended to this round's list; its size is summed.
+//   decrement     Alg. 2's update: one atomic decrement per member of each
+//                 newly covered set ...
+//   rebuild       ... or, when those members outnumber the members of the
+//                 sets still uncovered, the counts are rebuilt from the
+//                 uncovered sets (Sec. IV-C adaptive counter update).
+// The decrement/rebuild choice is taken on the device from the round's
+// volumes, so no host round trip is needed; both give the same counts.
+#include "imm_internal.cuh"
+
+namespace imm {
+
+constexpr int kModeDecrement = 0;
+constexpr int kModeRebuild = 1;
+
+__device__ __forceinline__ uint64_t shfl64s(uint64_t x, int srcLane)
+{
+    const uint32_t lo = __shfl_sync(kFull, (uint32_t)x, srcLane);
+    const uint32_t hi = __shfl_sync(kFull, (uint32_t)(x >> 32), srcLane);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint32_t owner_lane(uint32_t j, uint32_t incl)
+{
+    uint32_t o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t c = __shfl_sync(kFull, incl, o + step - 1);
+        if (c <= j) o += step;
+    }
+    return o;
+}
+
+// Every member u of the sets given by (start, len) per lane gets
+// atomicAdd(&work[u], delta).  Warp-cooperative: sets of >= 32 members one at
+// a time across the warp, shorter ones flattened across lanes.
+__device__ __forceinline__ void warp_apply_sets(const uint32_t* arena, uint64_t start, uint32_t len, uint32_t* work,
+                                                uint32_t delta)
+{
+    const int lane = threadIdx.x & 31;
+    const bool big = len >= 32;
+    uint32_t bigmask = __ballot_sync(kFull, big);
+    while (bigmask) {
+        const int o = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        const uint32_t L = __shfl_sync(kFull, len, o);
+        const uint64_t A = shfl64s(start, o);
+        for (uint32_t i = lane; i < L; i += 32) atomicAdd(&work[arena[A + i]], delta);
+    }
+    const uint32_t sl = big ? 0u : len;
+    uint32_t incl = sl;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - sl;
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t o = owner_lane(j, incl);
+        const uint64_t A = shfl64s(start, o);
+        const uint32_t ex = __shfl_sync(kFull, excl, o);
+        if (j < total) atomicAdd(&work[arena[A + (j - ex)]], delta);
+    }
+}
+
+// Decrement when the newly covered sets hold fewer members than a recount
+// would read: vol_cov <= members still uncovered afterwards + n/8 + sets/8.
+__device__ int round_mode(const SelectState& s, uint32_t j)
+{
+    uint64_t before = 0;
+    for (uint32_t i = 0; i < j; ++i) before += s.vol_cov[i];
+    const uint64_t cov = s.vol_cov[j];
+    const uint64_t unc_after = s.total_members - before - cov;
+    const uint64_t rebuild_cost = unc_after + (s.n >> 3) + (s.nsets >> 3);
+    return cov > rebuild_cost ? kModeRebuild : kModeDecrement;
+}
+
+__global__ void __launch_bounds__(256)
+argmax_kernel(const uint32_t* work, const uint8_t* picked, uint32_t n, unsigned long long* out)
+{
+    __shared__ unsigned long long s_best[8];
+    unsigned long long best = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (!picked[v]) {
+            const unsigned long long key = ((unsigned long long)work[v] << 32) | (0xFFFFFFFFu - v);
+            best = key > best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+        best = o > best ? o : best;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_best[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+        best = lane < (int)(blockDim.x >> 5) ? s_best[lane] : 0ull;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+            best = o > best ? o : best;
+        }
+        if (lane == 0 && best) atomicMax(out, best);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+cover_kernel(SelectState s, uint32_t j)
+{
+    const unsigned long long key = s.keys[j];
+    const uint32_t v = 0xFFFFFFFFu - (uint32_t)key;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s.picked[v] = 1;
+        s.seeds[j] = v;
+    }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long vol = 0;
+    for (uint32_t g = 0; g < s.nsegs; ++g) {
+        const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
+        const uint32_t* inv = s.segs[g].inv;
+        for (uint64_t i = a + tid; i < b; i += stride) {
+            const uint32_t sid = inv[i];
+            // a set holds v at most once, so only this thread can see sid here
+            if (!s.covered[sid]) {
+                s.covered[sid] = 1;
+                const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
+                s.newly[p] = sid;
+                vol += s.off[(uint64_t)sid + 1] - s.off[sid];
+            }
+        }
+    }
+    if (vol) atomicAdd(&s.vol_cov[j], vol);
+}
+
+__global__ void __launch_bounds__(256)
+decrement_kernel(SelectState s, uint32_t j)
+{
+    __shared__ int s_mode;
+    if (threadIdx.x == 0) s_mode = round_mode(s, j);
+    __syncthreads();
+    if (s_mode != kModeDecrement) return;
+    const uint64_t cnt = s.newly_n[j];
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t first = gw * 32; first < cnt; first += nw * 32) {
+        const uint64_t i = first + lane;
+        uint64_t start = 0;
+        uint32_t len = 0;
+        if (i < cnt) {
+            const uint32_t sid = s.newly[i];
+            start = s.off[sid];
+            len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+        }
+        warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);  // += -1
+    }
+}
+
+__global__ void __launch_bounds__(256)
+rebuild_zero_kernel(SelectState s, uint32_t j)
+{
+    __shared__ int s_mode;
+    if (threadIdx.x == 0) s_mode = round_mode(s, j);
+    __syncthreads();
+    if (s_mode != kModeRebuild) return;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) s.work[v] = 0;
+}
+
+__global__ void __launch_bounds__(256)
+rebuild_add_kernel(SelectState s, uint32_t j)
+{
+    __shared__ int s_mode;
+    if (threadIdx.x == 0) s_mode = round_mode(s, j);
+    __syncthreads();
+    if (s_mode != kModeRebuild) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t first = gw * 32; first < s.nsets; first += nw * 32) {
+        const uint64_t sid = first + lane;
+        uint64_t start = 0;
+        uint32_t len = 0;
+        if (sid < s.nsets && !s.covered[sid]) {
+            start = s.off[sid];
+            len = (uint32_t)(s.off[sid + 1] - start);
+        }
+        warp_apply_sets(s.arena, start, len, s.work, 1u);
+    }
+}
+
+cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
+                                uint64_t* launches)
+{
+    const uint32_t sms = (uint32_t)di.sms;
+    uint32_t ab = (s.n + 255) / 256;
+    if (ab > sms * 4) ab = sms * 4;
+    argmax_kernel<<<ab, 256, 0, st>>>(s.work, s.picked, s.n, s.keys + j);
+    cover_kernel<<<sms * 2, 256, 0, st>>>(s, j);
+    decrement_kernel<<<sms * 8, 256, 0, st>>>(s, j);
+    uint32_t zb = (s.n + 255) / 256;
+    if (zb > sms * 4) zb = sms * 4;
+    rebuild_zero_kernel<<<zb, 256, 0, st>>>(s, j);
+    uint64_t rb = (s.nsets + 255) / 256;
+    if (rb > sms * 8) rb = sms * 8;
+    if (rb == 0) rb = 1;
+    rebuild_add_kernel<<<(unsigned)rb, 256, 0, st>>>(s, j);
+    if (launches) *launches += 5;
+    return cudaGetLastError();
+}
+
+}  // namespace imm

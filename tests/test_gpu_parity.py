@@ -1,0 +1,287 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+Integer work is compared bit for bit: every RRR set (as a sorted member list
+per set id), the per-vertex occurrence counts, the seed sequence, covered
+counts, the theta ladder, LB and theta.  Sizes span several tiles, ragged
+tails, the warp path, the CTA path (shared-memory and global bitmaps), the
+LT long-walk path, staging overflow with resampling, and degenerate graphs."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from gpu_common import assert_same_stream, edges_to_graph, oracle_for
+
+pytestmark = pytest.mark.gpu
+
+IC, LT = graphgen.IC, graphgen.LT
+
+
+@pytest.fixture(scope="module")
+def imm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2411_09473_gb300 import imm as mod
+    return mod
+
+
+def new_ctx(imm, g):
+    ctx = imm.imm_create(device=0)
+    imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, g.weight, g.model)
+    return ctx
+
+
+def check_stream(imm, ctx, g, theta, seed, o=None):
+    imm.imm_sample(ctx, g.model, theta, seed)
+    if o is None:
+        o = oracle_for(g)
+    o.sample(theta, seed)
+    goff, gmem = imm.imm_get_sets(ctx, 0, theta)
+    ooff, omem = o.arena()
+    assert_same_stream(goff, gmem, ooff, omem)
+    assert np.array_equal(imm.imm_get_counts(ctx, g.n), o.counts())
+    return o
+
+
+def rand_graph(n, m, seed, model, p=None):
+    rng = np.random.default_rng(seed)
+    edges = set()
+    while len(edges) < m:
+        u, v = (int(x) for x in rng.integers(0, n, 2))
+        if u != v:
+            edges.add((u, v))
+    edges = sorted(edges)
+    if model == IC:
+        w = rng.uniform(0, 1, m) if p is None else np.full(m, p)
+    else:
+        indeg = np.bincount([v for (_, v) in edges], minlength=n)
+        w = [0.9 / indeg[v] for (_, v) in edges]
+    return edges_to_graph(n, edges, list(w), model)
+
+
+# ---------------------------------------------------------------------------
+# sampling
+# ---------------------------------------------------------------------------
+
+def test_ic_weighted_cascade_all_sets(imm):
+    g = graphgen.plain_workload("ic_wc_4k").graph
+    ctx = new_ctx(imm, g)
+    check_stream(imm, ctx, g, 6000, 1)
+
+
+def test_lt_rmat_all_sets(imm):
+    g = graphgen.make_graph(4096, 32768, 3, LT, "inv_indeg")
+    ctx = new_ctx(imm, g)
+    check_stream(imm, ctx, g, 20000, 3)
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_fuzz_small_graphs(imm, case):
+    rng = np.random.default_rng(1000 + case)
+    n = int(rng.integers(3, 700))
+    m = int(rng.integers(0, min(n * (n - 1), 6 * n)))
+    model = IC if case % 2 == 0 else LT
+    g = rand_graph(n, m, case, model)
+    ctx = new_ctx(imm, g)
+    seed = int(rng.integers(0, 2**63))
+    check_stream(imm, ctx, g, int(rng.integers(1, 3000)), seed)
+
+
+@pytest.mark.parametrize("n,m,gseed,pmax", [(3000, 24000, 11, 0.3), (1 << 14, 1 << 17, 12, 0.1),
+                                            (5000, 20000, 13, 1.0)])
+def test_ic_rmat_giant_sets(imm, n, m, gseed, pmax):
+    # high edge probabilities: many sets outgrow a warp and go to the CTA path
+    g = graphgen.make_graph(n, m, gseed, IC, "uniform", pmax=pmax)
+    ctx = new_ctx(imm, g)
+    check_stream(imm, ctx, g, 1500, gseed)
+
+
+def test_ic_p1_closures_and_star_hub(imm):
+    # star: vertex 0 has 5000 in-neighbours, all with p = 1; every set rooted at 0
+    # is the whole star (CTA path), the others are {leaf}
+    n = 5001
+    edges = [(i, 0) for i in range(1, n)]
+    g = edges_to_graph(n, edges, [1.0] * (n - 1), IC)
+    ctx = new_ctx(imm, g)
+    check_stream(imm, ctx, g, 30000, 8)
+
+
+def test_edgeless_and_p0_graphs(imm):
+    n = 777
+    g = graphgen.Graph(n=n, row=np.zeros(n + 1, dtype=np.uint64), src=np.zeros(0, dtype=np.uint32),
+                       weight=np.zeros(0, dtype=np.float32), model=IC)
+    ctx = new_ctx(imm, g)
+    check_stream(imm, ctx, g, 2000, 5)
+    g0 = rand_graph(300, 1500, 4, IC, p=0.0)
+    ctx = new_ctx(imm, g0)
+    check_stream(imm, ctx, g0, 1000, 6)
+    gl = graphgen.Graph(n=n, row=np.zeros(n + 1, dtype=np.uint64), src=np.zeros(0, dtype=np.uint32),
+                        weight=np.zeros(0, dtype=np.float32), model=LT)
+    ctx = new_ctx(imm, gl)
+    check_stream(imm, ctx, gl, 2000, 5)
+
+
+def test_lt_long_walks(imm):
+    # directed path and cycle with w = 1: walks far longer than the per-lane
+    # path capacity take the long-walk path
+    n = 3000
+    path = edges_to_graph(n, [(i, i + 1) for i in range(n - 1)], [1.0] * (n - 1), LT)
+    ctx = new_ctx(imm, path)
+    check_stream(imm, ctx, path, 400, 2)
+    cyc = edges_to_graph(1000, [(i, (i + 1) % 1000) for i in range(1000)], [1.0] * 1000, LT)
+    ctx = new_ctx(imm, cyc)
+    check_stream(imm, ctx, cyc, 300, 3)
+
+
+def test_stream_extension_is_prefix_stable(imm):
+    g = graphgen.make_graph(2048, 16384, 21, IC, "uniform", pmax=0.2)
+    a = new_ctx(imm, g)
+    imm.imm_sample(a, IC, 100, 9)
+    imm.imm_sample(a, IC, 2500, 9)
+    b = new_ctx(imm, g)
+    imm.imm_sample(b, IC, 2500, 9)
+    oa, ma = imm.imm_get_sets(a, 0, 2500)
+    ob, mb = imm.imm_get_sets(b, 0, 2500)
+    assert_same_stream(oa, ma, ob, mb)
+    assert np.array_equal(imm.imm_get_counts(a, g.n), imm.imm_get_counts(b, g.n))
+
+
+def test_ic_global_bitmap_path(imm):
+    # n = 2^21: the n-bit visited bitmap no longer fits in shared memory, so the
+    # CTA path keeps it in a per-CTA global slot; compare sampled set ids
+    n, m = 1 << 21, 1 << 23
+    g = graphgen.make_graph(n, m, 31, IC, "uniform", pmax=0.1)
+    ctx = new_ctx(imm, g)
+    theta = 1200
+    imm.imm_sample(ctx, IC, theta, 31)
+    off, mem = imm.imm_get_sets(ctx, 0, theta)
+    sizes = np.diff(off.astype(np.int64))
+    big = np.nonzero(sizes > 256)[0]
+    assert len(big) > 10
+    o = oracle_for(g)
+    rng = np.random.default_rng(0)
+    ids = list(big[:12]) + list(rng.choice(theta, 40, replace=False))
+    for s in ids:
+        want = o.sample_one(31, int(s))
+        got = np.sort(mem[off[s]:off[s + 1]])
+        assert np.array_equal(got, want), s
+
+
+# ---------------------------------------------------------------------------
+# selection and the IMM driver
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("model,k", [(IC, 10), (IC, 64), (LT, 25)])
+def test_select_matches_oracle(imm, model, k):
+    g = graphgen.make_graph(4096, 32768, 41, model, "inv_indeg")
+    ctx = new_ctx(imm, g)
+    o = check_stream(imm, ctx, g, 8000, 41)
+    seeds, cov = imm.imm_select(ctx, k)
+    want, wcov = o.select(k)
+    assert np.array_equal(seeds, want) and cov == wcov
+
+
+def test_select_k_equals_n_and_empty_stream(imm):
+    g = rand_graph(40, 120, 5, IC)
+    ctx = new_ctx(imm, g)
+    seeds, cov = imm.imm_select(ctx, 40)                 # no sets at all
+    assert seeds.tolist() == list(range(40)) and cov == 0
+    o = check_stream(imm, ctx, g, 500, 77)
+    seeds, cov = imm.imm_select(ctx, 40)
+    want, wcov = o.select(40)
+    assert np.array_equal(seeds, want) and cov == wcov == 500
+
+
+def check_run(imm, g, k, eps, ell, seed):
+    ctx = new_ctx(imm, g)
+    seeds, st = imm.imm_run(ctx, g.model, k, eps, ell, seed)
+    o = oracle_for(g)
+    want, ost = o.run(k, eps, ell, seed)
+    assert np.array_equal(seeds, want)
+    assert st.rounds == ost.rounds and st.stopped_early == ost.stopped_early
+    for i in range(st.rounds):
+        assert st.theta_i[i] == ost.theta_i[i]
+        assert st.covered_i[i] == ost.covered_i[i]
+        assert st.sets_i[i] == ost.sets_i[i]
+    assert st.lb == ost.lb and st.theta == ost.theta
+    assert st.num_sets == ost.num_sets and st.covered == ost.covered
+    assert st.lambda_prime == ost.lambda_prime and st.lambda_star == ost.lambda_star
+    assert np.array_equal(imm.imm_get_counts(ctx, g.n), o.counts())
+    goff, gmem = imm.imm_get_sets(ctx, 0, st.num_sets)
+    ooff, omem = o.arena()
+    assert_same_stream(goff, gmem, ooff, omem)
+    return st
+
+
+def test_run_ic_weighted_cascade_4k(imm):
+    w = graphgen.plain_workload("ic_wc_4k")
+    check_run(imm, w.graph, w.k, w.epsilon, w.ell, w.seed)
+
+
+def test_run_lt_small(imm):
+    g = graphgen.make_graph(8192, 65536, 7, LT, "inv_indeg")
+    check_run(imm, g, 20, 0.3, 1.0, 7)
+
+
+def test_run_ic_uniform_small(imm):
+    g = graphgen.make_graph(3000, 30000, 8, IC, "uniform", pmax=0.1)
+    check_run(imm, g, 7, 0.4, 1.0, 8)
+
+
+def test_run_no_early_stop(imm):
+    n = 64
+    g = graphgen.Graph(n=n, row=np.zeros(n + 1, dtype=np.uint64), src=np.zeros(0, dtype=np.uint32),
+                       weight=np.zeros(0, dtype=np.float32), model=IC)
+    st = check_run(imm, g, 2, 0.5, 1.0, 3)
+    assert st.stopped_early == 0 and st.lb == 1.0
+
+
+# ---------------------------------------------------------------------------
+# errors leave the context usable
+# ---------------------------------------------------------------------------
+
+def test_errors(imm):
+    g = graphgen.make_graph(1024, 8192, 2, IC, "inv_indeg")
+    ctx = new_ctx(imm, g)
+    with pytest.raises(imm.ImmError) as e:
+        imm.imm_sample(ctx, LT, 10, 1)
+    assert e.value.code == imm.IMM_EINVAL
+    imm.imm_sample(ctx, IC, 10, 1)
+    with pytest.raises(imm.ImmError) as e:
+        imm.imm_sample(ctx, IC, 20, 2)                # other seed, same stream
+    assert e.value.code == imm.IMM_ESTATE
+    with pytest.raises(imm.ImmError) as e:
+        imm.imm_select(ctx, 0)
+    assert e.value.code == imm.IMM_EINVAL
+    with pytest.raises(imm.ImmError) as e:
+        imm.imm_select(ctx, 1025)
+    assert e.value.code == imm.IMM_EINVAL
+    bad = g.src.copy()
+    bad[5] = 5000
+    with pytest.raises(imm.ImmError) as e:
+        imm.imm_load_graph(ctx, g.n, g.m, g.row, bad, g.weight, IC)
+    assert e.value.code == imm.IMM_EINVAL
+    w = g.weight.copy()
+    w[0] = np.float32("nan")
+    with pytest.raises(imm.ImmError):
+        imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, w, IC)
+    lt_over = graphgen.make_graph(1024, 8192, 2, LT, "inv_indeg")
+    w2 = lt_over.weight * np.float32(1.5)
+    with pytest.raises(imm.ImmError):
+        imm.imm_load_graph(ctx, g.n, g.m, lt_over.row, lt_over.src, np.minimum(w2, 1), LT)
+    # context still usable after the errors
+    imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, g.weight, IC)
+    o = check_stream(imm, ctx, g, 300, 4)
+    assert o.num_sets == 300
+
+
+def test_arena_limit_enomem_then_recovers(imm):
+    g = graphgen.make_graph(4096, 32768, 5, IC, "uniform", pmax=0.5)
+    ctx = new_ctx(imm, g)
+    imm.imm_set_arena_limit(ctx, 1 << 16)
+    with pytest.raises(imm.ImmError) as e:
+        imm.imm_sample(ctx, IC, 5000, 5)
+    assert e.value.code == imm.IMM_ENOMEM
+    imm.imm_set_arena_limit(ctx, 0)
+    imm.imm_reset_sets(ctx)
+    check_stream(imm, ctx, g, 2000, 5)
