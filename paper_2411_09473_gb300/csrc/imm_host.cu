@@ -59,17 +59,25 @@ struct imm_ctx {
     uint64_t nmembers = 0;
     DBuf off;   // uint64 [off_cap + 1]
     uint64_t off_cap = 0;
-    DBuf arena;  // uint32 [arena_cap]
+    DBuf arena;  // uint32 [arena_cap]: member lists of list-stored sets
     uint64_t arena_cap = 0;
-    DBuf cnt;  // uint32 [n]
+    uint64_t list_members = 0;
+    DBuf set_bmp;  // uint32 [off_cap]: bitmap id of each set, or kEmpty
+    DBuf bmp;      // bitmap arena: words uint32 per bitmap-stored set
+    DBuf bmp_set, bmp_len;  // uint32 [bmp_cap]
+    uint64_t bmp_cap = 0, nbmp = 0;
+    DBuf cnt;       // uint32 [n]: occurrences over all sets
+    DBuf cnt_list;  // uint32 [n]: occurrences over list-stored sets (index sizes)
     std::vector<Segment> segs;
     uint64_t index_bytes = 0;
 
     // sampling scratch
-    DBuf set_len, set_pos, set_edges, large_q;
+    DBuf set_len, set_pos, set_edges, set_kind, large_q, bmp_rel;
     uint32_t batch_cap = 0;
     DBuf stage;
     uint64_t stage_cap = 0;
+    DBuf big;
+    uint64_t big_cap = 0;
     DBuf scalars;
     DBuf scan_tmp;
     DBuf slot_q, slot_bm;
@@ -78,7 +86,7 @@ struct imm_ctx {
     DBuf hist, cursor, vtmp;
 
     // selection scratch
-    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, seeds, dsegs;
+    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, vol_list, bmp_cov, seeds, dsegs;
 
     DBuf flags;
     uint64_t arena_limit = 0;
@@ -216,10 +224,13 @@ void drop_stream(imm_ctx* c)
     c->have_stream = false;
     c->nsets = 0;
     c->nmembers = 0;
+    c->list_members = 0;
+    c->nbmp = 0;
     c->avg_len = 0.0;
     c->next_batch = 1u << 22;
     if (c->off.p) cudaMemsetAsync(c->off.p, 0, sizeof(uint64_t), c->stream);
     if (c->cnt.p) cudaMemsetAsync(c->cnt.p, 0, (size_t)c->n * 4, c->stream);
+    if (c->cnt_list.p) cudaMemsetAsync(c->cnt_list.p, 0, (size_t)c->n * 4, c->stream);
 }
 
 void free_graph(imm_ctx* c)
@@ -229,6 +240,7 @@ void free_graph(imm_ctx* c)
     dfree(c, c->src);
     dfree(c, c->thr);
     dfree(c, c->cnt);
+    dfree(c, c->cnt_list);
     dfree(c, c->hist);
     dfree(c, c->cursor);
     dfree(c, c->vtmp);
@@ -309,7 +321,10 @@ int load_graph_common(imm_ctx* c, uint32_t n, uint64_t m, const void* row, const
     c->model = model;
     TRY(dalloc(c, c->cnt, (size_t)n * 4));
     CK(cudaMemsetAsync(c->cnt.p, 0, (size_t)n * 4, c->stream));
+    TRY(dalloc(c, c->cnt_list, (size_t)n * 4));
+    CK(cudaMemsetAsync(c->cnt_list.p, 0, (size_t)n * 4, c->stream));
     TRY(dalloc(c, c->off, 8 * 1024));
+    TRY(dalloc(c, c->set_bmp, 4 * 1024));
     c->off_cap = 1023;
     CK(cudaMemsetAsync(c->off.p, 0, 8, c->stream));
     c->loaded = true;
@@ -334,7 +349,7 @@ int ensure_slots(imm_ctx* c, uint32_t want_slots, bool need_bitmap)
 int index_limit_ok(imm_ctx* c, uint64_t more_bytes)
 {
     if (!c->arena_limit) return IMM_OK;
-    const uint64_t used = c->arena_cap * 4 + c->index_bytes;
+    const uint64_t used = c->arena_cap * 4 + c->index_bytes + c->bmp.bytes;
     if (used + more_bytes > c->arena_limit)
         return set_err(c, IMM_ENOMEM, "arena limit of %llu bytes reached", (unsigned long long)c->arena_limit);
     return IMM_OK;
@@ -353,9 +368,9 @@ int merge_segments(imm_ctx* c)
     seg.set_begin = 0;
     seg.set_end = c->nsets;
     TRY(dalloc(c, seg.voff, ((size_t)c->n + 1) * 8));
-    TRY(dalloc(c, seg.inv, std::max<uint64_t>(c->nmembers, 1) * 4));
-    CK(launch_vertex_scan(P<uint32_t>(c->cnt), c->n, P<uint64_t>(seg.voff), nullptr, P<uint32_t>(c->cursor),
-                          P<uint64_t>(c->vtmp), c->di, c->stream));
+    TRY(dalloc(c, seg.inv, std::max<uint64_t>(c->list_members, 1) * 4));
+    CK(launch_vertex_scan(P<uint32_t>(c->cnt_list), c->n, P<uint64_t>(seg.voff), nullptr, nullptr,
+                          P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di, c->stream));
     CK(launch_index_scatter(0, c->nsets, P<uint64_t>(c->off), P<uint32_t>(c->arena), P<uint64_t>(seg.voff),
                             P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di, c->stream));
     c->acc_launches += 4;
@@ -375,7 +390,7 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
     c->seed = seed;
     const DevGraph g = dev_graph(c);
     const bool ic = c->model == IMM_IC;
-    const uint64_t words = ((uint64_t)c->n + 31) / 32;
+    const uint32_t words = (uint32_t)(((uint64_t)c->n + 31) / 32);
     TRY(ensure(c, c->scalars, sizeof(BatchScalars)));
     TRY(ensure(c, c->hist, (size_t)c->n * 4));
     TRY(ensure(c, c->cursor, (size_t)c->n * 4));
@@ -383,24 +398,7 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
 
     while (c->nsets < theta) {
         const uint64_t want = theta - c->nsets;
-        // Staging holds the members of one batch.  Its size follows the mean
-        // set size seen so far (at least one whole-graph set, at most 1.5e9
-        // members or an eighth of free memory); the batch takes as many sets
-        // as are expected to fit with 30% headroom.
-        const double avg = c->avg_len > 0 ? c->avg_len : 64.0;
-        {
-            const uint64_t floor_cap = (uint64_t)c->n + 4096;
-            const uint64_t fr = device_free_bytes() + c->stage.bytes;
-            const uint64_t stage_max = std::max<uint64_t>(floor_cap, std::min<uint64_t>(1500000000ull, fr / 8 / 4));
-            const double ideal = avg * 1.3 * (double)std::min<uint64_t>(want, c->next_batch);
-            const uint64_t need = std::max<uint64_t>(floor_cap, (uint64_t)std::min(ideal, (double)stage_max));
-            if (c->stage_cap < need) {
-                TRY(dalloc(c, c->stage, need * 4));
-                c->stage_cap = need;
-            }
-        }
-        uint64_t fit = (uint64_t)((double)c->stage_cap / (avg * 1.3));
-        uint32_t count = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(want, c->next_batch), std::max<uint64_t>(fit, 1));
+        uint32_t count = (uint32_t)std::min<uint64_t>(want, c->next_batch);
         if (count == 0) count = 1;
         // batch buffers
         if (c->batch_cap < count) {
@@ -408,15 +406,24 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
             TRY(dalloc(c, c->set_len, (size_t)cap * 4));
             TRY(dalloc(c, c->set_pos, (size_t)cap * 8));
             TRY(dalloc(c, c->set_edges, (size_t)cap * 4));
+            TRY(dalloc(c, c->set_kind, (size_t)cap * 4));
             TRY(dalloc(c, c->large_q, (size_t)cap * 4));
+            TRY(dalloc(c, c->bmp_rel, (size_t)cap * 4));
             TRY(dalloc(c, c->scan_tmp, scan_tmp_words(cap) * 8));
             c->batch_cap = cap;
         }
-        // arena offsets: room for base + count + 1 entries
+        // small-path staging: every small set holds at most small_cap members
+        const uint64_t stage_need = (uint64_t)count * small_cap(c->model);
+        if (c->stage_cap < stage_need) {
+            TRY(ensure(c, c->stage, stage_need * 4));
+            c->stage_cap = c->stage.bytes / 4;
+        }
+        // per-set arrays of the stream: room for base + count sets
         if (c->off_cap < c->nsets + count) {
             const uint64_t need = c->nsets + count;
             const uint64_t cap = std::max(need, c->off_cap + c->off_cap / 2);
             TRY(grow_keep(c, c->off, (cap + 1) * 8, (c->nsets + 1) * 8));
+            TRY(grow_keep(c, c->set_bmp, cap * 4, c->nsets * 4));
             c->off_cap = cap;
         }
 
@@ -427,11 +434,15 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
         b.seed = seed;
         b.base = c->nsets;
         b.count = count;
+        b.words = words;
         b.set_len = P<uint32_t>(c->set_len);
         b.set_pos = P<uint64_t>(c->set_pos);
         b.set_edges = P<uint32_t>(c->set_edges);
+        b.set_kind = P<uint32_t>(c->set_kind);
         b.stage = P<uint32_t>(c->stage);
         b.stage_cap = c->stage_cap;
+        b.big = P<uint32_t>(c->big);
+        b.big_cap = 0;
         b.large_q = P<uint32_t>(c->large_q);
         b.sc = sc;
 
@@ -446,6 +457,18 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
         c->acc_sample_launches += 1;
         c->acc_launches += 1;
         if (large_count) {
+            // outputs of the large path: a list or a bitmap of `words` words
+            // each; capped by a memory budget (sets past the cap are resampled)
+            const uint64_t fr = device_free_bytes() + c->big.bytes;
+            const uint64_t budget = std::max<uint64_t>((uint64_t)words * 4,
+                                                       std::min<uint64_t>(fr / 4, 16ull << 30) / 4);
+            const uint64_t need = std::min<uint64_t>((uint64_t)large_count * words, budget);
+            if (c->big_cap < need) {
+                TRY(ensure(c, c->big, need * 4));
+                c->big_cap = c->big.bytes / 4;
+            }
+            b.big = P<uint32_t>(c->big);
+            b.big_cap = c->big_cap;
             LargeSlots ls;
             if (ic) {
                 const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
@@ -465,8 +488,17 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
             c->acc_sample_launches += 1;
             c->acc_launches += 1;
         }
+        BatchOut o;
+        o.off = P<uint64_t>(c->off);
+        o.arena = P<uint32_t>(c->arena);
+        o.set_bmp = P<uint32_t>(c->set_bmp);
+        o.bmp = P<uint32_t>(c->bmp);
+        o.bmp_set = P<uint32_t>(c->bmp_set);
+        o.bmp_len = P<uint32_t>(c->bmp_len);
+        o.bmp_rel = P<uint32_t>(c->bmp_rel);
+        o.bmp_base = c->nbmp;
         CK(cudaEventRecord(c->ev[2], c->stream));
-        CK(launch_batch_scan(b, P<uint64_t>(c->off), P<uint64_t>(c->scan_tmp), c->di, c->stream));
+        CK(launch_batch_scan(b, o, P<uint64_t>(c->scan_tmp), c->di, c->stream));
         c->acc_launches += 3;
         BatchScalars hs;
         CK(cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
@@ -474,54 +506,68 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
         if (large_count) c->acc_sample_ms += elapsed(c, 0, 1);
         if (hs.error) return set_err(c, IMM_ECUDA, "sampler reported device error 0x%x", hs.error);
         const uint64_t committed = hs.committed;
-        const uint64_t bm = hs.members;
+        const uint64_t lm = hs.list_members;
+        const uint64_t nb = hs.nbitmaps;
         if (committed == 0) {
-            if (count == 1) return set_err(c, IMM_ENOMEM, "staging buffer cannot hold one RRR set");
+            if (count == 1) return set_err(c, IMM_ENOMEM, "output buffer cannot hold one RRR set");
             c->next_batch = std::max<uint32_t>(1, count / 4);
-            c->avg_len = std::max(c->avg_len * 2.0, (double)hs.stage_cursor / (double)count);
             continue;
         }
-        // arena + this segment's index
-        const uint64_t seg_bytes = ((uint64_t)c->n + 1) * 8 + bm * 4;
-        if (c->arena_cap < c->nmembers + bm) {
-            const uint64_t need = c->nmembers + bm;
+        // arena for the lists, bitmap arena, this batch's index segment
+        const uint64_t seg_bytes = ((uint64_t)c->n + 1) * 8 + lm * 4;
+        const uint64_t bmp_bytes = nb * words * 4;
+        if (c->arena_cap < c->list_members + lm) {
+            const uint64_t need = c->list_members + lm;
             uint64_t cap = std::max(need, c->arena_cap + c->arena_cap / 2);
-            if (c->arena_limit && (cap * 4 + c->index_bytes + seg_bytes > c->arena_limit)) cap = need;
-            TRY(index_limit_ok(c, (cap - c->arena_cap) * 4 + seg_bytes));
-            TRY(grow_keep(c, c->arena, cap * 4, c->nmembers * 4));
+            if (c->arena_limit && (cap * 4 + c->index_bytes + c->bmp.bytes + seg_bytes + bmp_bytes > c->arena_limit))
+                cap = need;
+            TRY(index_limit_ok(c, (cap - c->arena_cap) * 4 + seg_bytes + bmp_bytes));
+            TRY(grow_keep(c, c->arena, cap * 4, c->list_members * 4));
             c->arena_cap = cap;
         } else {
-            TRY(index_limit_ok(c, seg_bytes));
+            TRY(index_limit_ok(c, seg_bytes + bmp_bytes));
         }
+        if (c->bmp_cap < c->nbmp + nb) {
+            const uint64_t need = c->nbmp + nb;
+            const uint64_t cap = std::max(need, c->bmp_cap + c->bmp_cap / 2);
+            TRY(grow_keep(c, c->bmp, cap * words * 4, c->nbmp * words * 4));
+            TRY(grow_keep(c, c->bmp_set, cap * 4, c->nbmp * 4));
+            TRY(grow_keep(c, c->bmp_len, cap * 4, c->nbmp * 4));
+            c->bmp_cap = cap;
+        }
+        o.arena = P<uint32_t>(c->arena);
+        o.bmp = P<uint32_t>(c->bmp);
+        o.bmp_set = P<uint32_t>(c->bmp_set);
+        o.bmp_len = P<uint32_t>(c->bmp_len);
         Segment seg;
         seg.set_begin = c->nsets;
         seg.set_end = c->nsets + committed;
         TRY(dalloc(c, seg.voff, ((size_t)c->n + 1) * 8));
-        if (dalloc(c, seg.inv, std::max<uint64_t>(bm, 1) * 4) != IMM_OK) {
+        if (dalloc(c, seg.inv, std::max<uint64_t>(lm, 1) * 4) != IMM_OK) {
             dfree(c, seg.voff);
             return IMM_ENOMEM;
         }
         CK(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n * 4, c->stream));
-        CK(launch_compact(b, committed, P<uint64_t>(c->off), P<uint32_t>(c->arena), P<uint32_t>(c->hist), c->di,
-                          c->stream));
+        CK(launch_compact(b, o, committed, P<uint32_t>(c->hist), c->di, c->stream));
+        CK(launch_bitmap_store(b, o, nb, c->n, P<uint32_t>(c->cnt), c->di, c->stream));
         CK(launch_vertex_scan(P<uint32_t>(c->hist), c->n, P<uint64_t>(seg.voff), P<uint32_t>(c->cnt),
-                              P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di, c->stream));
+                              P<uint32_t>(c->cnt_list), P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di,
+                              c->stream));
         CK(launch_index_scatter(seg.set_begin, seg.set_end, P<uint64_t>(c->off), P<uint32_t>(c->arena),
                                 P<uint64_t>(seg.voff), P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di,
                                 c->stream));
         CK(cudaEventRecord(c->ev[3], c->stream));
-        c->acc_launches += 5;
+        c->acc_launches += nb ? 7 : 5;
         c->index_bytes += seg.voff.bytes + seg.inv.bytes;
         c->segs.push_back(seg);
         c->nsets += committed;
-        c->nmembers += bm;
+        c->list_members += lm;
+        c->nmembers += hs.all_members;
+        c->nbmp += nb;
         c->acc_edges += hs.edges;
-        c->acc_sample_members += bm;
+        c->acc_sample_members += hs.all_members;
         CK(cudaEventSynchronize(c->ev[3]));
         c->acc_index_ms += elapsed(c, 2, 3);
-        // running mean set size (drives the next batch's staging)
-        const double len = (double)bm / (double)committed;
-        c->avg_len = c->avg_len > 0 ? 0.5 * (c->avg_len + len) : len;
         c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : (1u << 22);
         if (c->segs.size() > 48) TRY(merge_segments(c));
     }
@@ -541,6 +587,8 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     TRY(ensure(c, c->keys, (size_t)k * 8));
     TRY(ensure(c, c->newly_n, (size_t)k * 8));
     TRY(ensure(c, c->vol_cov, (size_t)k * 8));
+    TRY(ensure(c, c->vol_list, (size_t)k * 8));
+    TRY(ensure(c, c->bmp_cov, (size_t)k * 8));
     TRY(ensure(c, c->seeds, (size_t)k * 4));
     std::vector<DevSegment> hsegs;
     for (auto& s : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(s.voff), P<uint32_t>(s.inv)});
@@ -556,13 +604,22 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     CK(cudaMemsetAsync(c->keys.p, 0, (size_t)k * 8, c->stream));
     CK(cudaMemsetAsync(c->newly_n.p, 0, (size_t)k * 8, c->stream));
     CK(cudaMemsetAsync(c->vol_cov.p, 0, (size_t)k * 8, c->stream));
+    CK(cudaMemsetAsync(c->vol_list.p, 0, (size_t)k * 8, c->stream));
+    CK(cudaMemsetAsync(c->bmp_cov.p, 0, (size_t)k * 8, c->stream));
 
     SelectState s;
     s.n = c->n;
+    s.words = (uint32_t)(((uint64_t)c->n + 31) / 32);
     s.nsets = R;
     s.total_members = c->nmembers;
+    s.list_members = c->list_members;
     s.off = P<uint64_t>(c->off);
     s.arena = P<uint32_t>(c->arena);
+    s.set_bmp = P<uint32_t>(c->set_bmp);
+    s.bmp = P<uint32_t>(c->bmp);
+    s.bmp_set = P<uint32_t>(c->bmp_set);
+    s.bmp_len = P<uint32_t>(c->bmp_len);
+    s.nbmp = (uint32_t)c->nbmp;
     s.work = P<uint32_t>(c->work);
     s.picked = P<uint8_t>(c->picked);
     s.covered = P<uint8_t>(c->covered);
@@ -570,6 +627,8 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     s.keys = P<unsigned long long>(c->keys);
     s.newly_n = P<unsigned long long>(c->newly_n);
     s.vol_cov = P<unsigned long long>(c->vol_cov);
+    s.vol_list = P<unsigned long long>(c->vol_list);
+    s.bmp_cov = P<unsigned long long>(c->bmp_cov);
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
@@ -638,9 +697,11 @@ void imm_destroy(imm_ctx* c)
     if (!c) return;
     DeviceGuard guard(c->device);
     free_graph(c);
-    DBuf* bufs[] = {&c->off,     &c->arena,   &c->set_len, &c->set_pos, &c->set_edges, &c->large_q,
-                    &c->stage,   &c->scalars, &c->scan_tmp, &c->covered, &c->newly,    &c->keys,
-                    &c->newly_n, &c->vol_cov, &c->seeds,    &c->dsegs,   &c->flags};
+    DBuf* bufs[] = {&c->off,      &c->arena,   &c->set_len,  &c->set_pos, &c->set_edges, &c->set_kind,
+                    &c->large_q,  &c->bmp_rel, &c->stage,    &c->big,     &c->scalars,   &c->scan_tmp,
+                    &c->covered,  &c->newly,   &c->keys,     &c->newly_n, &c->vol_cov,   &c->vol_list,
+                    &c->bmp_cov,  &c->seeds,   &c->dsegs,    &c->flags,   &c->set_bmp,   &c->bmp,
+                    &c->bmp_set,  &c->bmp_len};
     for (DBuf* b : bufs) dfree(c, *b);
     cudaStreamSynchronize(c->stream);
     for (auto& e : c->ev)
@@ -792,22 +853,47 @@ int imm_run(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint6
     return IMM_OK;
 }
 
+// Members of one stored set, sorted ascending (lists are sorted here, bitmaps
+// are expanded in id order).
+static int fetch_set(imm_ctx* c, uint64_t id, std::vector<uint32_t>& out)
+{
+    uint64_t o[2];
+    uint32_t bid = kEmpty;
+    CK(cudaMemcpyAsync(o, P<uint64_t>(c->off) + id, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&bid, P<uint32_t>(c->set_bmp) + id, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out.clear();
+    if (bid == kEmpty) {
+        out.resize(o[1] - o[0]);
+        if (!out.empty()) {
+            CK(cudaMemcpyAsync(out.data(), P<uint32_t>(c->arena) + o[0], out.size() * 4, cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        std::sort(out.begin(), out.end());
+    } else {
+        const uint64_t words = ((uint64_t)c->n + 31) / 32;
+        std::vector<uint32_t> bits(words);
+        CK(cudaMemcpyAsync(bits.data(), P<uint32_t>(c->bmp) + (uint64_t)bid * words, words * 4,
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (uint64_t w = 0; w < words; ++w)
+            for (uint32_t x = bits[w]; x; x &= x - 1) out.push_back((uint32_t)(w * 32 + __builtin_ctz(x)));
+    }
+    return IMM_OK;
+}
+
 int imm_get_set(imm_ctx* c, uint64_t set_id, uint32_t* buf, uint32_t cap, uint32_t* len)
 {
     if (!c) return IMM_EINVAL;
     DeviceGuard guard(c->device);
     if (set_id >= c->nsets || !len) return set_err(c, IMM_EINVAL, "set id out of range");
-    uint64_t o[2];
-    CK(cudaMemcpyAsync(o, P<uint64_t>(c->off) + set_id, 16, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    const uint64_t L = o[1] - o[0];
-    *len = (uint32_t)L;
-    if (L > cap || (L && !buf)) return set_err(c, IMM_EINVAL, "set has %llu members, cap %u", (unsigned long long)L, cap);
-    if (L) {
-        CK(cudaMemcpyAsync(buf, P<uint32_t>(c->arena) + o[0], L * 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        std::sort(buf, buf + L);
-    }
+    std::vector<uint32_t> m;
+    TRY(fetch_set(c, set_id, m));
+    *len = (uint32_t)m.size();
+    if (m.size() > cap || (!m.empty() && !buf))
+        return set_err(c, IMM_EINVAL, "set has %zu members, cap %u", m.size(), cap);
+    std::copy(m.begin(), m.end(), buf);
     return IMM_OK;
 }
 
@@ -815,16 +901,44 @@ int imm_get_sets(imm_ctx* c, uint64_t first, uint64_t count, uint64_t* off_out, 
 {
     if (!c) return IMM_EINVAL;
     DeviceGuard guard(c->device);
-    if (first > c->nsets || count > c->nsets - first || !off_out) return set_err(c, IMM_EINVAL, "range outside the stream");
-    CK(cudaMemcpyAsync(off_out, P<uint64_t>(c->off) + first, (count + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (first > c->nsets || count > c->nsets - first || !off_out)
+        return set_err(c, IMM_EINVAL, "range outside the stream");
+    std::vector<uint64_t> lo(count + 1);
+    std::vector<uint32_t> bid(count ? count : 1);
+    CK(cudaMemcpyAsync(lo.data(), P<uint64_t>(c->off) + first, (count + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (count)
+        CK(cudaMemcpyAsync(bid.data(), P<uint32_t>(c->set_bmp) + first, count * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    const uint64_t a = off_out[0], b = off_out[count];
-    for (uint64_t i = 0; i <= count; ++i) off_out[i] -= a;
-    if (b - a > cap || (b > a && !mem_out)) return set_err(c, IMM_EINVAL, "range holds %llu members, cap %llu",
-                                                          (unsigned long long)(b - a), (unsigned long long)cap);
-    if (b > a) {
-        CK(cudaMemcpyAsync(mem_out, P<uint32_t>(c->arena) + a, (b - a) * 4, cudaMemcpyDeviceToHost, c->stream));
+    // true sizes: list lengths, and bitmap sizes for bitmap-stored sets
+    std::vector<uint32_t> blen(count ? count : 1, 0);
+    for (uint64_t i = 0; i < count; ++i) {
+        if (bid[i] != kEmpty) {
+            CK(cudaMemcpyAsync(&blen[i], P<uint32_t>(c->bmp_len) + bid[i], 4, cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    off_out[0] = 0;
+    for (uint64_t i = 0; i < count; ++i)
+        off_out[i + 1] = off_out[i] + (bid[i] == kEmpty ? lo[i + 1] - lo[i] : (uint64_t)blen[i]);
+    const uint64_t total = off_out[count];
+    if (total > cap || (total && !mem_out))
+        return set_err(c, IMM_EINVAL, "range holds %llu members, cap %llu", (unsigned long long)total,
+                       (unsigned long long)cap);
+    // lists in stored (traversal) order, bitmaps expanded in id order
+    std::vector<uint32_t> lists(lo[count] - lo[0]);
+    if (!lists.empty()) {
+        CK(cudaMemcpyAsync(lists.data(), P<uint32_t>(c->arena) + lo[0], lists.size() * 4, cudaMemcpyDeviceToHost,
+                           c->stream));
         CK(cudaStreamSynchronize(c->stream));
+    }
+    std::vector<uint32_t> tmp;
+    for (uint64_t i = 0; i < count; ++i) {
+        if (bid[i] == kEmpty) {
+            std::copy(lists.begin() + (lo[i] - lo[0]), lists.begin() + (lo[i + 1] - lo[0]), mem_out + off_out[i]);
+        } else {
+            TRY(fetch_set(c, first + i, tmp));
+            std::copy(tmp.begin(), tmp.end(), mem_out + off_out[i]);
+        }
     }
     return IMM_OK;
 }

@@ -71,25 +71,34 @@ struct BatchScalars {
     uint32_t cursor;        // next batch-relative set id for the small-set path
     uint32_t large_count;   // sets handed to the large-set path
     uint32_t large_cursor;  // next entry of the large-set queue
-    uint32_t first_fail;    // lowest batch-relative id whose staging reservation failed
-    unsigned long long stage_cursor;
-    unsigned long long edges;      // IC: in-edges whose coin was read; LT: walk steps
-    unsigned long long committed;  // sets kept (min(first_fail, count)), by the scan
-    unsigned long long members;    // members of the kept sets, by the scan
+    uint32_t first_fail;    // lowest batch-relative id whose output reservation failed
+    unsigned long long stage_cursor;  // small-set staging (exact capacity)
+    unsigned long long big_cursor;    // large-set outputs (lists or bitmaps)
+    unsigned long long edges;         // IC: in-edges of the members; LT: walk steps
+    unsigned long long committed;     // sets kept (min(first_fail, count)), by the scan
+    unsigned long long list_members;  // members of kept sets stored as lists
+    unsigned long long all_members;   // members of all kept sets
+    unsigned long long nbitmaps;      // kept sets stored as bitmaps
     int error;
     int pad;
 };
 
+constexpr uint64_t kBigFlag = 1ull << 63;  // set_pos points into the large-output buffer
+
 struct SampleBatch {
     uint64_t seed;
-    uint64_t base;      // first set id of the batch
-    uint32_t count;     // sets in the batch
-    uint32_t* set_len;  // [count]
-    uint64_t* set_pos;  // [count] staging offset
+    uint64_t base;        // first set id of the batch
+    uint32_t count;       // sets in the batch
+    uint32_t words;       // ceil(n / 32): words of one n-bit bitmap
+    uint32_t* set_len;    // [count] members
+    uint64_t* set_pos;    // [count] output position (kBigFlag: large-output buffer)
     uint32_t* set_edges;  // [count] IC: in-edges of the members; LT: walk steps
-    uint32_t* stage;    // staging members
+    uint32_t* set_kind;   // [count] 0 = member list, 1 = n-bit bitmap
+    uint32_t* stage;      // small-set member lists
     uint64_t stage_cap;
-    uint32_t* large_q;  // [count] batch-relative ids for the large-set path
+    uint32_t* big;        // large-set outputs
+    uint64_t big_cap;
+    uint32_t* large_q;    // [count] batch-relative ids for the large-set path
     BatchScalars* sc;
 };
 
@@ -103,12 +112,23 @@ struct LargeSlots {
     uint32_t nslots;
 };
 
-// One segment of the inverted index: sets [set_begin, set_end) whose
-// members were scattered by vertex: inv[voff[v] .. voff[v+1]) = ids of the
-// segment's sets that contain v.
+// One segment of the inverted index over the list-stored sets of one batch:
+// inv[voff[v] .. voff[v+1]) = ids of the segment's sets that contain v.
 struct DevSegment {
     const uint64_t* voff;
     const uint32_t* inv;
+};
+
+// Where the batch's kept sets go once the scan has run.
+struct BatchOut {
+    uint64_t* off;        // stream list offsets (off[base .. base+committed])
+    uint32_t* arena;      // stream member lists
+    uint32_t* set_bmp;    // [nsets] bitmap id of each set, kEmpty for lists
+    uint32_t* bmp;        // bitmap arena, `words` words per bitmap
+    uint32_t* bmp_set;    // [nbmp] set id of each bitmap
+    uint32_t* bmp_len;    // [nbmp] members of each bitmap set
+    uint32_t* bmp_rel;    // [count] batch-relative id of the batch's r-th bitmap
+    uint64_t bmp_base;    // bitmaps stored before this batch
 };
 
 // ---------------------------------------------------------------------------
@@ -126,6 +146,7 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
                               uint32_t* thr, int* d_flags, cudaStream_t st);
 
 // sampling
+uint32_t small_cap(int model);  // members a small-path set may hold (staging per set)
 int ic_large_uses_smem(uint32_t n, const DeviceInfo& di);
 cudaError_t launch_ic_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
 cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
@@ -133,14 +154,22 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
 cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
                            const DeviceInfo& di, cudaStream_t st);
-// exclusive scan of the kept sets' lengths into off[base+1 ..]; needs tmp of
-// scan_tmp_words(count) uint64
+// Scan of the kept sets: list offsets into off[], bitmap ranks, totals.
 uint64_t scan_tmp_words(uint32_t count);
-cudaError_t launch_batch_scan(const SampleBatch& b, uint64_t* off, uint64_t* tmp, const DeviceInfo& di,
+cudaError_t launch_batch_scan(const SampleBatch& b, const BatchOut& o, uint64_t* tmp, const DeviceInfo& di,
                               cudaStream_t st);
-cudaError_t launch_compact(const SampleBatch& b, uint64_t committed, const uint64_t* off, uint32_t* arena,
-                           uint32_t* seg_hist, const DeviceInfo& di, cudaStream_t st);
-cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff, uint32_t* cnt,
+cudaError_t launch_compact(const SampleBatch& b, const BatchOut& o, uint64_t committed, uint32_t* seg_hist,
+                           const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_bitmap_store(const SampleBatch& b, const BatchOut& o, uint64_t nbitmaps, uint32_t n,
+                                uint32_t* cnt, const DeviceInfo& di, cudaStream_t st);
+// cnt[v] += number of bitmaps first .. first+count-1 holding v, skipping
+// bitmaps whose set is flagged in skip[] (nullable)
+cudaError_t launch_bitmap_count(const uint32_t* bmp, uint32_t words, uint32_t n, uint64_t first, uint64_t count,
+                                const uint8_t* skip, const uint32_t* bmp_set, uint32_t* cnt, const DeviceInfo& di,
+                                cudaStream_t st);
+// voff = exclusive scan of hist; cnt[v] += hist[v] and cnt2[v] += hist[v]
+// (each nullable); cursor zeroed
+cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff, uint32_t* cnt, uint32_t* cnt2,
                                uint32_t* cursor, uint64_t* tmp, const DeviceInfo& di, cudaStream_t st);
 cudaError_t launch_index_scatter(uint64_t set_begin, uint64_t set_end, const uint64_t* off,
                                  const uint32_t* arena, const uint64_t* voff, uint32_t* cursor,
@@ -149,10 +178,17 @@ cudaError_t launch_index_scatter(uint64_t set_begin, uint64_t set_end, const uin
 // selection
 struct SelectState {
     uint32_t n;
+    uint32_t words;
     uint64_t nsets;
-    uint64_t total_members;
+    uint64_t total_members;   // all members (lists and bitmaps)
+    uint64_t list_members;    // members of list-stored sets
     const uint64_t* off;
     const uint32_t* arena;
+    const uint32_t* set_bmp;  // [nsets] bitmap id or kEmpty
+    const uint32_t* bmp;      // bitmap arena
+    const uint32_t* bmp_set;  // [nbmp]
+    const uint32_t* bmp_len;  // [nbmp]
+    uint32_t nbmp;
     uint32_t* work;      // n mutable counts
     uint8_t* picked;     // n
     uint8_t* covered;    // nsets
@@ -160,6 +196,8 @@ struct SelectState {
     unsigned long long* keys;      // k: packed (count, ~v) argmax per round
     unsigned long long* newly_n;   // k: sets covered per round
     unsigned long long* vol_cov;   // k: members of the sets covered per round
+    unsigned long long* vol_list;  // k: of which in list-stored sets
+    unsigned long long* bmp_cov;   // k: bitmap sets covered per round
     uint32_t* seeds;     // k
     const DevSegment* segs;
     uint32_t nsegs;

@@ -1,16 +1,23 @@
 // RRR-set sampling kernels (Generate_RRRsets, EfficientIMM Alg. 3) and the
-// prefix-sum compaction of the sampled sets into the device arena.
+// storage of the sampled sets.
 //
 // A batch of consecutive set ids is sampled in two passes:
 //   small path  one warp per set (IC) or one lane per walk (LT); the visited
 //               state lives in shared memory (open-addressing hash / path
 //               list).  A set that outgrows it is handed to the large path.
-//   large path  one CTA per set (IC) with an n-bit visited bitmap in shared
-//               memory when it fits, else in a per-CTA global slot; one thread
-//               per walk (LT) with a global bitmap.
-// Each finished set is written to a staging buffer; the batch scan turns the
-// set lengths into arena offsets and the compaction kernel copies members to
-// the arena in set-id order while counting occurrences (Alg. 3 fused count).
+//   large path  one CTA per set (IC): level-synchronous BFS whose warps claim
+//               32-vertex chunks of the frontier; vertices with >= 32 in-edge
+//               quads are swept by the whole warp, the rest are flattened
+//               across lanes.  The n-bit visited bitmap sits in shared memory
+//               when it fits, else in a per-CTA global slot.  LT long walks
+//               run one per thread with a global bitmap.
+// Storage follows the adaptive representation of Sec. IV-C: a set is kept
+// as a member list unless its list would be larger than an n-bit bitmap, in
+// which case the bitmap is kept (O(1) membership tests during selection).
+// The batch scan turns list lengths into arena offsets (prefix-sum
+// compaction); the compaction kernel copies lists into the arena in set-id
+// order while counting occurrences, and bitmap sets are counted by a
+// column-popcount kernel (Alg. 3's fused count).
 #include "imm_internal.cuh"
 
 namespace imm {
@@ -36,17 +43,42 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
-__device__ __forceinline__ uint4 load_thr4(const uint32_t* thr, uint64_t quad)
+__device__ __forceinline__ uint4 load_thr4(const uint32_t* thr, uint32_t quad)
 {
     return __ldg(reinterpret_cast<const uint4*>(thr) + quad);
 }
 
-// Reserve staging space for a finished set.  On overflow the set is marked
-// failed; it and every later set of the batch are resampled by the next batch.
-__device__ __forceinline__ bool reserve_stage(const SampleBatch& b, uint32_t rel, uint32_t len, uint64_t* pos)
+// in-edge range of v (m < 2^32, so the offsets fit 32 bits)
+__device__ __forceinline__ void edge_range(const DevGraph& g, uint32_t v, uint32_t& rs, uint32_t& re)
+{
+    rs = (uint32_t)__ldg(g.row + v);
+    re = (uint32_t)__ldg(g.row + v + 1);
+}
+
+__device__ __forceinline__ uint32_t quads_of(uint32_t rs, uint32_t re)
+{
+    return re > rs ? ((re - 1) >> 2) - (rs >> 2) + 1 : 0u;
+}
+
+// IC coins of the four in-edges of `quad` for set (s_hi, s_lo), restricted
+// to [rs, re): bit t is set iff edge 4*quad + t is live.
+__device__ __forceinline__ uint32_t live_mask(uint4 w, uint4 th, uint32_t quad, uint32_t rs, uint32_t re)
+{
+    uint32_t live = ((w.x >> 8) < th.x ? 1u : 0u) | ((w.y >> 8) < th.y ? 2u : 0u) |
+                    ((w.z >> 8) < th.z ? 4u : 0u) | ((w.w >> 8) < th.w ? 8u : 0u);
+    const uint32_t e0 = quad << 2;
+    if (e0 < rs) live &= 0xFu << (rs - e0);
+    if (e0 + 4 > re) live &= 0xFu >> (e0 + 4 - re);
+    return live & 0xFu;
+}
+
+// Reserve space in the small-set staging (its capacity is exact, so failure
+// means a bookkeeping bug and is reported through the error word).
+__device__ __forceinline__ bool reserve_small(const SampleBatch& b, uint32_t rel, uint32_t len, uint64_t* pos)
 {
     const unsigned long long p = atomicAdd(&b.sc->stage_cursor, (unsigned long long)len);
     if (p + len > b.stage_cap) {
+        atomicOr(&b.sc->error, kErrQueue);
         b.set_len[rel] = kLenFailed;
         atomicMin(&b.sc->first_fail, rel);
         return false;
@@ -54,6 +86,27 @@ __device__ __forceinline__ bool reserve_stage(const SampleBatch& b, uint32_t rel
     *pos = p;
     b.set_pos[rel] = p;
     b.set_len[rel] = len;
+    b.set_kind[rel] = 0;
+    return true;
+}
+
+// Reserve space for a large set's output (list of len members, or a bitmap
+// of b.words words).  When the buffer is full the set is marked failed; it
+// and every later set of the batch are resampled by the next batch.
+__device__ __forceinline__ bool reserve_big(const SampleBatch& b, uint32_t rel, uint32_t len, uint32_t kind,
+                                            uint64_t* pos)
+{
+    const uint64_t size = kind ? (uint64_t)b.words : (uint64_t)len;
+    const unsigned long long p = atomicAdd(&b.sc->big_cursor, (unsigned long long)size);
+    if (p + size > b.big_cap) {
+        b.set_len[rel] = kLenFailed;
+        atomicMin(&b.sc->first_fail, rel);
+        return false;
+    }
+    *pos = p;
+    b.set_pos[rel] = p | kBigFlag;
+    b.set_len[rel] = len;
+    b.set_kind[rel] = kind;
     return true;
 }
 
@@ -64,6 +117,13 @@ constexpr int kSmallWarps = 8;
 constexpr uint32_t kSmallCap = 256;          // members a warp keeps before handing off
 constexpr int kSmallHashBits = 9;
 constexpr uint32_t kSmallHash = 1u << kSmallHashBits;  // > kSmallCap + 4*32 (one inner step)
+
+constexpr uint32_t kLtCap = 48;               // path length a lane keeps before handing off
+
+uint32_t small_cap(int model)
+{
+    return model == 0 ? kSmallCap : kLtCap;
+}
 
 __device__ __forceinline__ uint32_t small_slot(uint32_t v)
 {
@@ -104,19 +164,16 @@ ic_small_kernel(DevGraph g, SampleBatch b)
         __syncwarp();
 
         uint32_t head = 0, tail = 1;
-        uint64_t edges = 0;  // lane-partial sum of in-degrees of expanded members
+        uint32_t edges = 0;  // lane-partial sum of in-degrees of expanded members
         bool overflow = false;
         while (head < tail && !overflow) {
             // Up to 32 frontier vertices; their in-edge quads are flattened
             // across the warp so short and long adjacency lists share lanes.
             const uint32_t nf = min(tail - head, 32u);
-            uint64_t rs = 0, re = 0;
-            uint32_t nq = 0;
+            uint32_t rs = 0, re = 0, nq = 0;
             if ((uint32_t)lane < nf) {
-                const uint32_t v = list[head + lane];
-                rs = g.row[v];
-                re = g.row[v + 1];
-                if (re > rs) nq = (uint32_t)(((re - 1) >> 2) - (rs >> 2) + 1);
+                edge_range(g, list[head + lane], rs, re);
+                nq = quads_of(rs, re);
                 edges += re - rs;
             }
             uint32_t incl = nq;
@@ -137,28 +194,22 @@ ic_small_kernel(DevGraph g, SampleBatch b)
                     const uint32_t c = __shfl_sync(kFull, incl, o + step - 1);
                     if (c <= j) o += step;
                 }
-                const uint64_t ors = shfl64(rs, o);
-                const uint64_t ore = shfl64(re, o);
+                const uint32_t ors = __shfl_sync(kFull, rs, o);
+                const uint32_t ore = __shfl_sync(kFull, re, o);
                 const uint32_t oex = __shfl_sync(kFull, excl, o);
-                const bool active = j < total;
-                uint4 w = make_uint4(0, 0, 0, 0), th = make_uint4(0, 0, 0, 0);
-                uint64_t e0 = 0;
-                if (active) {
-                    const uint64_t quad = (ors >> 2) + (j - oex);
-                    e0 = quad << 2;
-                    w = philox(make_uint4(s_lo, s_hi, (uint32_t)quad, kTagIC), key);
-                    th = load_thr4(g.thr, quad);
+                uint32_t live = 0, quad = 0;
+                if (j < total) {
+                    quad = (ors >> 2) + (j - oex);
+                    const uint4 th = load_thr4(g.thr, quad);
+                    const uint4 w = philox(make_uint4(s_lo, s_hi, quad, kTagIC), key);
+                    live = live_mask(w, th, quad, ors, ore);
                 }
-                const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-                const uint32_t tv[4] = {th.x, th.y, th.z, th.w};
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const uint64_t e = e0 + t;
-                    const bool live = active && e >= ors && e < ore && (wv[t] >> 8) < tv[t];
                     bool isnew = false;
                     uint32_t u = 0, sl = 0;
-                    if (live) {
-                        u = __ldg(g.src + e);
+                    if ((live >> t) & 1u) {
+                        u = __ldg(g.src + (quad << 2) + t);
                         sl = small_slot(u);
                         uint32_t probe = 0;
                         for (; probe < kSmallHash; ++probe) {
@@ -202,8 +253,8 @@ ic_small_kernel(DevGraph g, SampleBatch b)
             uint64_t pos = 0;
             int ok = 0;
             if (lane == 0) {
-                b.set_edges[rel] = (uint32_t)edges;
-                ok = reserve_stage(b, rel, tail, &pos) ? 1 : 0;
+                b.set_edges[rel] = edges;
+                ok = reserve_small(b, rel, tail, &pos) ? 1 : 0;
             }
             ok = __shfl_sync(kFull, ok, 0);
             pos = shfl64(pos, 0);
@@ -229,19 +280,30 @@ cudaError_t launch_ic_small(const DevGraph& g, const SampleBatch& b, const Devic
 }
 
 // ===========================================================================
-// IC, large path: one CTA per set, queue-driven BFS.
+// IC, large path: one CTA per set, level-synchronous BFS.
 // ===========================================================================
 constexpr int kLargeThreads = 1024;
-constexpr int kLargeWarps = kLargeThreads / 32;
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
+// Test-and-set of u in the visited bitmap; appends u to the member queue when
+// it was not yet visited.  Bits only ever go from 0 to 1, so a plain read
+// that sees the bit set is final and saves the atomic.
+__device__ __forceinline__ void visit(uint32_t u, uint32_t* bm, uint32_t* q, uint32_t* s_tail)
 {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += t;
+    const uint32_t bit = 1u << (u & 31);
+    uint32_t* word = bm + (u >> 5);
+    if (*reinterpret_cast<volatile uint32_t*>(word) & bit) return;
+    const uint32_t old = atomicOr(word, bit);
+    if (!(old & bit)) q[atomicAdd(s_tail, 1u)] = u;
+}
+
+__device__ __forceinline__ void visit_live(uint32_t live, uint32_t quad, const uint32_t* src, uint32_t* bm,
+                                           uint32_t* q, uint32_t* s_tail)
+{
+    while (live) {
+        const int t = __ffs(live) - 1;
+        live &= live - 1;
+        visit(__ldg(src + (quad << 2) + t), bm, q, s_tail);
     }
-    return x;
 }
 
 template <bool kSmemBitmap>
@@ -249,28 +311,21 @@ __global__ void __launch_bounds__(kLargeThreads, 1)
 ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
 {
     extern __shared__ __align__(16) uint32_t dyn_bitmap[];
-    __shared__ uint64_t s_rs[kLargeThreads];
-    __shared__ uint64_t s_re[kLargeThreads];
-    __shared__ uint32_t s_excl[kLargeThreads + 1];
-    __shared__ uint32_t s_warp[kLargeWarps];
-    __shared__ uint32_t s_tail;
-    __shared__ uint32_t s_claim;
+    __shared__ uint32_t s_tail, s_next, s_end, s_claim;
     __shared__ int s_ok;
     __shared__ unsigned long long s_pos;
     __shared__ unsigned long long s_edges;
 
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31;
-    const int wid = tid >> 5;
-    const uint32_t ltm = lanemask_lt();
-    const uint64_t words = ((uint64_t)g.n + 31) >> 5;
+    const uint32_t words = b.words;
     uint32_t* bm = kSmemBitmap ? dyn_bitmap : ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
     const uint2 key = philox_key(b.seed);
     const uint32_t large_count = b.sc->large_count;  // final: written by the previous launch
 
     if (kSmemBitmap)
-        for (uint64_t i = tid; i < words; i += kLargeThreads) bm[i] = 0;
+        for (uint32_t i = tid; i < words; i += kLargeThreads) bm[i] = 0;
 
     for (;;) {
         if (tid == 0) {
@@ -288,104 +343,115 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
             q[0] = root;
             bm[root >> 5] |= 1u << (root & 31);
             s_tail = 1;
+            s_next = 0;
+            s_end = 1;
         }
         __syncthreads();
 
-        uint32_t head = 0, tail = 1;
-        uint64_t edges = 0;
-        while (head < tail) {
-            const uint32_t nf = min(tail - head, (uint32_t)kLargeThreads);
-            uint32_t nq = 0;
-            if (tid < nf) {
-                const uint32_t v = q[head + tid];
-                const uint64_t rs = g.row[v], re = g.row[v + 1];
-                s_rs[tid] = rs;
-                s_re[tid] = re;
-                if (re > rs) nq = (uint32_t)(((re - 1) >> 2) - (rs >> 2) + 1);
-                edges += re - rs;
-            }
-            const uint32_t incl = warp_incl_scan(nq, lane);
-            if (lane == 31) s_warp[wid] = incl;
-            __syncthreads();
-            if (wid == 0) {
-                const uint32_t x = warp_incl_scan(s_warp[lane], lane);
-                s_warp[lane] = x;
-            }
-            __syncthreads();
-            const uint32_t wbase = wid ? s_warp[wid - 1] : 0u;
-            s_excl[tid] = wbase + incl - nq;
-            const uint32_t total = s_warp[kLargeWarps - 1];
-            if (tid == 0) s_excl[kLargeThreads] = total;
-            __syncthreads();
-
-            for (uint32_t j0 = (uint32_t)wid * 32u; j0 < total; j0 += kLargeThreads) {
-                const uint32_t j = j0 + lane;
-                const bool active = j < total;
-                uint4 w = make_uint4(0, 0, 0, 0), th = make_uint4(0, 0, 0, 0);
-                uint64_t e0 = 0, ors = 0, ore = 0;
-                if (active) {
-                    // owner: last frontier slot whose exclusive prefix is <= j
-                    uint32_t lo = 0, hi = nf;
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (s_excl[mid] <= j) lo = mid;
-                        else hi = mid;
-                    }
-                    ors = s_rs[lo];
-                    ore = s_re[lo];
-                    const uint64_t quad = (ors >> 2) + (j - s_excl[lo]);
-                    e0 = quad << 2;
-                    w = philox(make_uint4(s_lo, s_hi, (uint32_t)quad, kTagIC), key);
-                    th = load_thr4(g.thr, quad);
+        uint32_t edges = 0;
+        uint32_t end = s_end;
+        for (;;) {
+            // one level: warps claim 32-vertex chunks of q[.. end)
+            for (;;) {
+                uint32_t c = 0;
+                if (lane == 0) c = atomicAdd(&s_next, 32u);
+                c = __shfl_sync(kFull, c, 0);
+                if (c >= end) break;
+                const uint32_t nf = min(end - c, 32u);
+                uint32_t rs = 0, re = 0, nq = 0;
+                if ((uint32_t)lane < nf) {
+                    edge_range(g, q[c + lane], rs, re);
+                    nq = quads_of(rs, re);
+                    edges += re - rs;
                 }
-                const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-                const uint32_t tv[4] = {th.x, th.y, th.z, th.w};
+                // vertices with >= 32 quads: the whole warp sweeps their quads
+                uint32_t bigm = __ballot_sync(kFull, nq >= 32);
+                while (bigm) {
+                    const int o = __ffs(bigm) - 1;
+                    bigm &= bigm - 1;
+                    const uint32_t ors = __shfl_sync(kFull, rs, o);
+                    const uint32_t ore = __shfl_sync(kFull, re, o);
+                    const uint32_t q1 = (ore - 1) >> 2;
+                    for (uint32_t qa = (ors >> 2) + lane; qa <= q1; qa += 64) {
+                        const uint32_t qb = qa + 32;
+                        const bool hb = qb <= q1;
+                        const uint4 tha = load_thr4(g.thr, qa);
+                        const uint4 thb = hb ? load_thr4(g.thr, qb) : make_uint4(0, 0, 0, 0);
+                        const uint4 wa = philox(make_uint4(s_lo, s_hi, qa, kTagIC), key);
+                        const uint4 wb = philox(make_uint4(s_lo, s_hi, qb, kTagIC), key);
+                        const uint32_t la = live_mask(wa, tha, qa, ors, ore);
+                        const uint32_t lb = hb ? live_mask(wb, thb, qb, ors, ore) : 0u;
+                        visit_live(la, qa, g.src, bm, q, &s_tail);
+                        visit_live(lb, qb, g.src, bm, q, &s_tail);
+                    }
+                }
+                // the rest: flattened across lanes
+                const uint32_t sq = nq >= 32 ? 0u : nq;
+                uint32_t incl = sq;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const uint64_t e = e0 + t;
-                    const bool live = active && e >= ors && e < ore && (wv[t] >> 8) < tv[t];
-                    bool isnew = false;
-                    uint32_t u = 0;
-                    if (live) {
-                        u = __ldg(g.src + e);
-                        const uint32_t bit = 1u << (u & 31);
-                        const uint32_t old = atomicOr(&bm[u >> 5], bit);
-                        isnew = (old & bit) == 0;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, incl, d);
+                    if (lane >= d) incl += t;
+                }
+                const uint32_t total = __shfl_sync(kFull, incl, 31);
+                const uint32_t excl = incl - sq;
+                for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    uint32_t o = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const uint32_t cc = __shfl_sync(kFull, incl, o + step - 1);
+                        if (cc <= j) o += step;
                     }
-                    const uint32_t nm = __ballot_sync(kFull, isnew);
-                    if (nm) {
-                        uint32_t base = 0;
-                        if (lane == 0) base = atomicAdd(&s_tail, (uint32_t)__popc(nm));
-                        base = __shfl_sync(kFull, base, 0);
-                        if (isnew) q[base + __popc(nm & ltm)] = u;
+                    const uint32_t ors = __shfl_sync(kFull, rs, o);
+                    const uint32_t ore = __shfl_sync(kFull, re, o);
+                    const uint32_t oex = __shfl_sync(kFull, excl, o);
+                    if (j < total) {
+                        const uint32_t quad = (ors >> 2) + (j - oex);
+                        const uint4 th = load_thr4(g.thr, quad);
+                        const uint4 w = philox(make_uint4(s_lo, s_hi, quad, kTagIC), key);
+                        visit_live(live_mask(w, th, quad, ors, ore), quad, g.src, bm, q, &s_tail);
                     }
                 }
             }
             __syncthreads();
-            head += nf;
-            tail = s_tail;
+            if (tid == 0) {
+                s_next = end;
+                s_end = s_tail;
+            }
+            __syncthreads();
+            const uint32_t ne = s_end;
+            if (ne == end) break;
+            end = ne;
         }
 
-        // set done: record, stage, clear the visited bits
+        // set done: record, store as list or bitmap, clear the visited bits
+        const uint32_t len = end;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) edges += __shfl_xor_sync(kFull, edges, d);
         if (lane == 0 && edges) atomicAdd(&s_edges, (unsigned long long)edges);
         __syncthreads();
+        const uint32_t kind = len > words ? 1u : 0u;
         if (tid == 0) {
             b.set_edges[rel] = (uint32_t)s_edges;
             uint64_t pos = 0;
-            s_ok = reserve_stage(b, rel, tail, &pos) ? 1 : 0;
+            s_ok = reserve_big(b, rel, len, kind, &pos) ? 1 : 0;
             s_pos = pos;
         }
         __syncthreads();
         if (s_ok) {
-            const uint64_t pos = s_pos;
-            for (uint32_t i = tid; i < tail; i += kLargeThreads) b.stage[pos + i] = q[i];
+            uint32_t* out = b.big + s_pos;
+            if (kind) {
+                for (uint32_t i = tid; i < words; i += kLargeThreads) out[i] = bm[i];
+            } else {
+                for (uint32_t i = tid; i < len; i += kLargeThreads) out[i] = q[i];
+            }
         }
-        if (kSmemBitmap || (uint64_t)tail * 8 >= words) {
-            for (uint64_t i = tid; i < words; i += kLargeThreads) bm[i] = 0;
+        __syncthreads();
+        if (kSmemBitmap || (uint64_t)len * 8 >= words) {
+            for (uint32_t i = tid; i < words; i += kLargeThreads) bm[i] = 0;
         } else {
-            for (uint32_t i = tid; i < tail; i += kLargeThreads) bm[q[i] >> 5] = 0;
+            for (uint32_t i = tid; i < len; i += kLargeThreads) bm[q[i] >> 5] = 0;
         }
         __syncthreads();
     }
@@ -399,10 +465,7 @@ static size_t large_smem_bytes(uint32_t n)
 
 int ic_large_uses_smem(uint32_t n, const DeviceInfo& di)
 {
-    // static shared memory of the kernel is ~20.7 KB; keep 1 KB of slack
-    const size_t static_bytes = sizeof(uint64_t) * 2 * kLargeThreads + sizeof(uint32_t) * (kLargeThreads + 1) +
-                                sizeof(uint32_t) * kLargeWarps + 64;
-    return large_smem_bytes(n) + static_bytes + 1024 <= (size_t)di.max_smem_optin;
+    return large_smem_bytes(n) + 4096 <= (size_t)di.max_smem_optin;
 }
 
 cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls, const DeviceInfo& di,
@@ -425,13 +488,12 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 // LT, small path: one lane per walk, path kept in shared memory.
 // ===========================================================================
 constexpr int kLtThreads = 128;
-constexpr uint32_t kLtCap = 48;
 
 // first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi
-__device__ __forceinline__ uint64_t lt_pick(const uint32_t* cthr, uint64_t lo, uint64_t hi, uint32_t r)
+__device__ __forceinline__ uint32_t lt_pick(const uint32_t* cthr, uint32_t lo, uint32_t hi, uint32_t r)
 {
     while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t mid = lo + ((hi - lo) >> 1);
         if (r < __ldg(cthr + mid)) hi = mid;
         else lo = mid + 1;
     }
@@ -474,8 +536,9 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         if (!busy) continue;
         // one step of the reverse walk at v
         const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), v, kTagLT), key);
-        const uint64_t lo = g.row[v], hi = g.row[v + 1];
-        const uint64_t pick = lt_pick(g.thr, lo, hi, w.x >> 8);
+        uint32_t lo, hi;
+        edge_range(g, v, lo, hi);
+        const uint32_t pick = lt_pick(g.thr, lo, hi, w.x >> 8);
         bool stop = pick == hi;
         uint32_t u = 0;
         if (!stop) {
@@ -500,7 +563,7 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         } else {
             b.set_edges[rel] = len;
             uint64_t pos = 0;
-            if (reserve_stage(b, rel, len, &pos))
+            if (reserve_small(b, rel, len, &pos))
                 for (uint32_t i = 0; i < len; ++i) b.stage[pos + i] = path[i][tid];
             busy = false;
         }
@@ -531,6 +594,7 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
     const uint2 key = philox_key(b.seed);
     const uint32_t large_count = b.sc->large_count;
+    const uint32_t words = b.words;
     for (;;) {
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(&b.sc->large_cursor, 1u);
@@ -546,8 +610,9 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
             len = 1;
             for (;;) {
                 const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), v, kTagLT), key);
-                const uint64_t lo = g.row[v], hi = g.row[v + 1];
-                const uint64_t pick = lt_pick(g.thr, lo, hi, w.x >> 8);
+                uint32_t lo, hi;
+                edge_range(g, v, lo, hi);
+                const uint32_t pick = lt_pick(g.thr, lo, hi, w.x >> 8);
                 if (pick == hi) break;
                 const uint32_t u = __ldg(g.src + pick);
                 const uint32_t bit = 1u << (u & 31);
@@ -559,14 +624,21 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
             b.set_edges[rel] = len;
         }
         len = __shfl_sync(kFull, len, 0);
+        __syncwarp();
+        const uint32_t kind = len > words ? 1u : 0u;
         uint64_t pos = 0;
         int ok = 0;
-        if (lane == 0) ok = reserve_stage(b, rel, len, &pos) ? 1 : 0;
+        if (lane == 0) ok = reserve_big(b, rel, len, kind, &pos) ? 1 : 0;
         ok = __shfl_sync(kFull, ok, 0);
         pos = shfl64(pos, 0);
+        if (ok) {
+            uint32_t* out = b.big + pos;
+            if (kind)
+                for (uint32_t i = lane; i < words; i += 32) out[i] = bm[i];
+            else
+                for (uint32_t i = lane; i < len; i += 32) out[i] = q[i];
+        }
         __syncwarp();
-        if (ok)
-            for (uint32_t i = lane; i < len; i += 32) b.stage[pos + i] = q[i];
         for (uint32_t i = lane; i < len; i += 32) bm[q[i] >> 5] = 0;
         __syncwarp();
     }
@@ -581,8 +653,8 @@ cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeS
 }
 
 // ===========================================================================
-// Batch scan: exclusive prefix of the kept sets' lengths -> arena offsets.
-// Kept sets are ids [0, committed), committed = min(first_fail, count).
+// Batch scan over the kept sets [0, committed), committed = min(first_fail,
+// count): list offsets into off[], bitmap ranks, and the batch totals.
 // ===========================================================================
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -600,7 +672,7 @@ __device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t x, int lane)
 
 uint64_t scan_tmp_words(uint32_t count)
 {
-    return 2 * ((uint64_t)count / kScanTile + 2) + 8;
+    return 4 * ((uint64_t)count / kScanTile + 2) + 8;
 }
 
 __device__ __forceinline__ uint32_t batch_committed(const SampleBatch& b)
@@ -630,101 +702,126 @@ __device__ uint64_t block_excl_scan64(uint64_t x, uint64_t* s_warp, uint64_t* to
     return wb + incl - x;
 }
 
+// per tile: [0] list members, [1] bitmap sets, [2] all members, [3] edges
 __global__ void __launch_bounds__(kScanThreads)
-batch_tile_sum_kernel(SampleBatch b, uint64_t* tile_len, uint64_t* tile_edges)
+batch_tile_sum_kernel(SampleBatch b, uint64_t* tiles, uint32_t ntiles)
 {
     __shared__ uint64_t s_warp[32];
     const uint32_t committed = batch_committed(b);
     const uint64_t t0 = (uint64_t)blockIdx.x * kScanTile;
-    uint64_t a = 0, ed = 0;
+    uint64_t sum[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const uint64_t r = t0 + (uint64_t)threadIdx.x * kScanItems + i;
         if (r < committed) {
-            a += b.set_len[r];
-            ed += b.set_edges[r];
+            const uint32_t len = b.set_len[r];
+            const uint32_t kind = b.set_kind[r];
+            sum[0] += kind ? 0u : len;
+            sum[1] += kind;
+            sum[2] += len;
+            sum[3] += b.set_edges[r];
         }
     }
-    uint64_t tot_a, tot_e;
-    block_excl_scan64(a, s_warp, &tot_a);
-    block_excl_scan64(ed, s_warp, &tot_e);
-    if (threadIdx.x == 0) {
-        tile_len[blockIdx.x] = tot_a;
-        tile_edges[blockIdx.x] = tot_e;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint64_t tot;
+        block_excl_scan64(sum[c], s_warp, &tot);
+        if (threadIdx.x == 0) tiles[(uint64_t)c * ntiles + blockIdx.x] = tot;
     }
 }
 
-// one block: exclusive scan of the tile sums, and the batch totals
+// one block: exclusive scans of the tile sums (lists, bitmaps) and totals
 __global__ void __launch_bounds__(kScanThreads)
-batch_tile_scan_kernel(SampleBatch b, uint64_t* tile_len, const uint64_t* tile_edges, uint32_t ntiles)
+batch_tile_scan_kernel(SampleBatch b, uint64_t* tiles, uint32_t ntiles)
 {
     __shared__ uint64_t s_warp[32];
-    __shared__ uint64_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
+    __shared__ uint64_t s_carry[2];
+    if (threadIdx.x < 2) s_carry[threadIdx.x] = 0;
     __syncthreads();
-    uint64_t edges = 0;
+    uint64_t all = 0, edges = 0;
     for (uint32_t t0 = 0; t0 < ntiles; t0 += kScanThreads) {
         const uint32_t t = t0 + threadIdx.x;
-        const uint64_t x = t < ntiles ? tile_len[t] : 0;
-        if (t < ntiles) edges += tile_edges[t];
-        uint64_t tot;
-        const uint64_t ex = block_excl_scan64(x, s_warp, &tot);
-        if (t < ntiles) tile_len[t] = s_carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
+        if (t < ntiles) {
+            all += tiles[2ull * ntiles + t];
+            edges += tiles[3ull * ntiles + t];
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint64_t x = t < ntiles ? tiles[(uint64_t)c * ntiles + t] : 0;
+            uint64_t tot;
+            const uint64_t ex = block_excl_scan64(x, s_warp, &tot);
+            if (t < ntiles) tiles[(uint64_t)c * ntiles + t] = s_carry[c] + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) s_carry[c] += tot;
+            __syncthreads();
+        }
     }
-    uint64_t tot_e;
-    block_excl_scan64(edges, s_warp, &tot_e);
+    uint64_t tot_all, tot_edges;
+    block_excl_scan64(all, s_warp, &tot_all);
+    block_excl_scan64(edges, s_warp, &tot_edges);
     if (threadIdx.x == 0) {
-        b.sc->members = s_carry;
+        b.sc->list_members = s_carry[0];
+        b.sc->nbitmaps = s_carry[1];
+        b.sc->all_members = tot_all;
+        b.sc->edges = tot_edges;
         b.sc->committed = batch_committed(b);
-        b.sc->edges = tot_e;
     }
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-batch_tile_write_kernel(SampleBatch b, const uint64_t* tile_off, uint64_t* off)
+batch_tile_write_kernel(SampleBatch b, BatchOut o, const uint64_t* tiles, uint32_t ntiles)
 {
     __shared__ uint64_t s_warp[32];
     const uint32_t committed = batch_committed(b);
     const uint64_t t0 = (uint64_t)blockIdx.x * kScanTile;
-    uint64_t v[kScanItems];
-    uint64_t a = 0;
+    uint32_t ln[kScanItems], kd[kScanItems];
+    uint64_t a = 0, c = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const uint64_t r = t0 + (uint64_t)threadIdx.x * kScanItems + i;
-        v[i] = r < committed ? b.set_len[r] : 0;
-        a += v[i];
+        ln[i] = 0;
+        kd[i] = 0;
+        if (r < committed) {
+            kd[i] = b.set_kind[r];
+            ln[i] = kd[i] ? 0u : b.set_len[r];
+        }
+        a += ln[i];
+        c += kd[i];
     }
     uint64_t tot;
     uint64_t ex = block_excl_scan64(a, s_warp, &tot);
-    const uint64_t base = off[b.base] + tile_off[blockIdx.x];
+    uint64_t exb = block_excl_scan64(c, s_warp, &tot);
+    const uint64_t base = o.off[b.base] + tiles[blockIdx.x];
+    const uint64_t bbase = tiles[(uint64_t)ntiles + blockIdx.x];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const uint64_t r = t0 + (uint64_t)threadIdx.x * kScanItems + i;
-        ex += v[i];
-        if (r < committed) off[b.base + r + 1] = base + ex;
+        if (r < committed) {
+            const uint64_t rank = bbase + exb;
+            o.set_bmp[b.base + r] = kd[i] ? (uint32_t)(o.bmp_base + rank) : kEmpty;
+            if (kd[i]) o.bmp_rel[rank] = (uint32_t)r;
+        }
+        ex += ln[i];
+        exb += kd[i];
+        if (r < committed) o.off[b.base + r + 1] = base + ex;
     }
 }
 
-cudaError_t launch_batch_scan(const SampleBatch& b, uint64_t* off, uint64_t* tmp, const DeviceInfo& di,
+cudaError_t launch_batch_scan(const SampleBatch& b, const BatchOut& o, uint64_t* tmp, const DeviceInfo& di,
                               cudaStream_t st)
 {
     (void)di;
     const uint32_t ntiles = (uint32_t)(((uint64_t)b.count + kScanTile - 1) / kScanTile);
-    uint64_t* tile_len = tmp;
-    uint64_t* tile_edges = tmp + ntiles + 1;
-    batch_tile_sum_kernel<<<ntiles, kScanThreads, 0, st>>>(b, tile_len, tile_edges);
-    batch_tile_scan_kernel<<<1, kScanThreads, 0, st>>>(b, tile_len, tile_edges, ntiles);
-    batch_tile_write_kernel<<<ntiles, kScanThreads, 0, st>>>(b, tile_len, off);
+    batch_tile_sum_kernel<<<ntiles, kScanThreads, 0, st>>>(b, tmp, ntiles);
+    batch_tile_scan_kernel<<<1, kScanThreads, 0, st>>>(b, tmp, ntiles);
+    batch_tile_write_kernel<<<ntiles, kScanThreads, 0, st>>>(b, o, tmp, ntiles);
     return cudaGetLastError();
 }
 
 // ===========================================================================
-// Compaction: staging -> arena in set-id order, fused occurrence count.
-// A warp takes 32 consecutive sets: sets of >= 32 members are copied by the
-// whole warp one at a time; the shorter ones are flattened across lanes.
+// Compaction of the list-stored sets: staging -> arena in set-id order, fused
+// occurrence count.  A warp takes 32 consecutive sets: sets of >= 32 members
+// are copied by the whole warp one at a time; the shorter ones are flattened.
 // ===========================================================================
 __device__ __forceinline__ uint32_t owner_of(uint32_t j, uint32_t incl)
 {
@@ -737,8 +834,13 @@ __device__ __forceinline__ uint32_t owner_of(uint32_t j, uint32_t incl)
     return o;
 }
 
+__device__ __forceinline__ const uint32_t* source_of(const SampleBatch& b, uint64_t pos)
+{
+    return (pos & kBigFlag) ? b.big + (pos & ~kBigFlag) : b.stage + pos;
+}
+
 __global__ void __launch_bounds__(256)
-compact_kernel(SampleBatch b, uint64_t committed, const uint64_t* off, uint32_t* arena, uint32_t* hist)
+compact_kernel(SampleBatch b, BatchOut ob, uint64_t committed, uint32_t* hist)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -746,11 +848,12 @@ compact_kernel(SampleBatch b, uint64_t committed, const uint64_t* off, uint32_t*
     for (uint64_t first = gw * 32; first < committed; first += nw * 32) {
         const uint64_t rel = first + lane;
         uint32_t len = 0;
-        uint64_t pos = 0, dst = 0;
-        if (rel < committed) {
+        const uint32_t* src = nullptr;
+        uint64_t dst = 0;
+        if (rel < committed && b.set_kind[rel] == 0) {
             len = b.set_len[rel];
-            pos = b.set_pos[rel];
-            dst = off[b.base + rel];
+            src = source_of(b, b.set_pos[rel]);
+            dst = ob.off[b.base + rel];
         }
         const bool big = len >= 32;
         uint32_t bigmask = __ballot_sync(kFull, big);
@@ -758,10 +861,11 @@ compact_kernel(SampleBatch b, uint64_t committed, const uint64_t* off, uint32_t*
             const int o = __ffs(bigmask) - 1;
             bigmask &= bigmask - 1;
             const uint32_t L = __shfl_sync(kFull, len, o);
-            const uint64_t P = shfl64(pos, o), D = shfl64(dst, o);
+            const uint32_t* S = reinterpret_cast<const uint32_t*>(shfl64(reinterpret_cast<uint64_t>(src), o));
+            const uint64_t D = shfl64(dst, o);
             for (uint32_t i = lane; i < L; i += 32) {
-                const uint32_t u = b.stage[P + i];
-                arena[D + i] = u;
+                const uint32_t u = S[i];
+                ob.arena[D + i] = u;
                 atomicAdd(&hist[u], 1u);
             }
         }
@@ -777,27 +881,102 @@ compact_kernel(SampleBatch b, uint64_t committed, const uint64_t* off, uint32_t*
         for (uint32_t j0 = 0; j0 < total; j0 += 32) {
             const uint32_t j = j0 + lane;
             const uint32_t o = owner_of(j, incl);
-            const uint64_t P = shfl64(pos, o), D = shfl64(dst, o);
+            const uint32_t* S = reinterpret_cast<const uint32_t*>(shfl64(reinterpret_cast<uint64_t>(src), o));
+            const uint64_t D = shfl64(dst, o);
             const uint32_t ex = __shfl_sync(kFull, excl, o);
             if (j < total) {
-                const uint32_t u = b.stage[P + (j - ex)];
-                arena[D + (j - ex)] = u;
+                const uint32_t u = S[j - ex];
+                ob.arena[D + (j - ex)] = u;
                 atomicAdd(&hist[u], 1u);
             }
         }
     }
 }
 
-cudaError_t launch_compact(const SampleBatch& b, uint64_t committed, const uint64_t* off, uint32_t* arena,
-                           uint32_t* hist, const DeviceInfo& di, cudaStream_t st)
+cudaError_t launch_compact(const SampleBatch& b, const BatchOut& o, uint64_t committed, uint32_t* hist,
+                           const DeviceInfo& di, cudaStream_t st)
 {
     if (committed == 0) return cudaSuccess;
-    uint64_t warps = (committed + 31) / 32;
+    const uint64_t warps = (committed + 31) / 32;
     uint64_t blocks = (warps + 7) / 8;
     const uint64_t cap = (uint64_t)di.sms * 16;
     if (blocks > cap) blocks = cap;
-    compact_kernel<<<(unsigned)blocks, 256, 0, st>>>(b, committed, off, arena, hist);
+    compact_kernel<<<(unsigned)blocks, 256, 0, st>>>(b, o, committed, hist);
     return cudaGetLastError();
+}
+
+// ===========================================================================
+// Bitmap-stored sets: copy into the bitmap arena, then count them into cnt[]
+// by columns (each thread owns 32 vertices of one bitmap word and sums the
+// bits of a chunk of bitmaps in registers).
+// ===========================================================================
+__global__ void __launch_bounds__(256)
+bitmap_copy_kernel(SampleBatch b, BatchOut o, uint64_t nbitmaps)
+{
+    for (uint64_t r = blockIdx.x; r < nbitmaps; r += gridDim.x) {
+        const uint32_t rel = o.bmp_rel[r];
+        const uint32_t* src = b.big + (b.set_pos[rel] & ~kBigFlag);
+        const uint64_t gid = o.bmp_base + r;
+        uint32_t* dst = o.bmp + gid * b.words;
+        for (uint32_t i = threadIdx.x; i < b.words; i += blockDim.x) dst[i] = src[i];
+        if (threadIdx.x == 0) {
+            o.bmp_set[gid] = (uint32_t)(b.base + rel);
+            o.bmp_len[gid] = b.set_len[rel];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+bitmap_count_kernel(const uint32_t* bmp, uint32_t words, uint32_t n, uint64_t first, uint64_t count,
+                    uint64_t per_chunk, const uint8_t* skip, const uint32_t* bmp_set, uint32_t* cnt)
+{
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t b0 = first + (uint64_t)blockIdx.y * per_chunk;
+    uint64_t b1 = b0 + per_chunk;
+    if (b1 > first + count) b1 = first + count;
+    if (w >= words) return;
+    uint32_t c[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) c[i] = 0;
+    for (uint64_t bi = b0; bi < b1; ++bi) {
+        if (skip && skip[bmp_set[bi]]) continue;
+        const uint32_t x = __ldg(bmp + bi * words + w);
+        if (!x) continue;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) c[i] += (x >> i) & 1u;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const uint32_t v = w * 32 + i;
+        if (c[i] && v < n) atomicAdd(&cnt[v], c[i]);
+    }
+}
+
+cudaError_t launch_bitmap_count(const uint32_t* bmp, uint32_t words, uint32_t n, uint64_t first, uint64_t count,
+                                const uint8_t* skip, const uint32_t* bmp_set, uint32_t* cnt, const DeviceInfo& di,
+                                cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    const uint32_t bx = (words + 255) / 256;
+    uint64_t chunks = ((uint64_t)di.sms * 8 + bx - 1) / bx;
+    if (chunks > count) chunks = count;
+    if (chunks > 65535) chunks = 65535;
+    if (chunks == 0) chunks = 1;
+    const uint64_t per = (count + chunks - 1) / chunks;
+    chunks = (count + per - 1) / per;
+    bitmap_count_kernel<<<dim3(bx, (unsigned)chunks), 256, 0, st>>>(bmp, words, n, first, count, per, skip, bmp_set,
+                                                                      cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap_store(const SampleBatch& b, const BatchOut& o, uint64_t nbitmaps, uint32_t n, uint32_t* cnt,
+                                const DeviceInfo& di, cudaStream_t st)
+{
+    if (nbitmaps == 0) return cudaSuccess;
+    uint64_t grid = nbitmaps;
+    if (grid > (uint64_t)di.sms * 8) grid = (uint64_t)di.sms * 8;
+    bitmap_copy_kernel<<<(unsigned)grid, 256, 0, st>>>(b, o, nbitmaps);
+    return launch_bitmap_count(o.bmp, b.words, n, o.bmp_base, nbitmaps, nullptr, nullptr, cnt, di, st);
 }
 
 // ===========================================================================
@@ -821,7 +1000,7 @@ vtx_tile_sum_kernel(const uint32_t* hist, uint32_t n, uint64_t* tile_sum)
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-tile_excl_scan_kernel(uint64_t* tile, uint32_t ntiles, uint64_t* grand_total)
+tile_excl_scan_kernel(uint64_t* tile, uint32_t ntiles)
 {
     __shared__ uint64_t s_warp[32];
     __shared__ uint64_t s_carry;
@@ -837,12 +1016,11 @@ tile_excl_scan_kernel(uint64_t* tile, uint32_t ntiles, uint64_t* grand_total)
         if (threadIdx.x == 0) s_carry += tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0 && grand_total) *grand_total = s_carry;
 }
 
 __global__ void __launch_bounds__(kScanThreads)
 vtx_tile_write_kernel(const uint32_t* hist, uint32_t n, const uint64_t* tile_off, uint64_t* voff, uint32_t* cnt,
-                      uint32_t* cursor)
+                      uint32_t* cnt2, uint32_t* cursor)
 {
     __shared__ uint64_t s_warp[32];
     const uint64_t t0 = (uint64_t)blockIdx.x * kScanTile;
@@ -862,6 +1040,7 @@ vtx_tile_write_kernel(const uint32_t* hist, uint32_t n, const uint64_t* tile_off
         if (v < n) {
             voff[v] = ex;
             if (cnt) cnt[v] += h[i];
+            if (cnt2) cnt2[v] += h[i];
             cursor[v] = 0;
         }
         ex += h[i];
@@ -869,20 +1048,21 @@ vtx_tile_write_kernel(const uint32_t* hist, uint32_t n, const uint64_t* tile_off
     }
 }
 
-cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff, uint32_t* cnt, uint32_t* cursor,
-                               uint64_t* tmp, const DeviceInfo& di, cudaStream_t st)
+cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff, uint32_t* cnt, uint32_t* cnt2,
+                               uint32_t* cursor, uint64_t* tmp, const DeviceInfo& di, cudaStream_t st)
 {
     (void)di;
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + kScanTile - 1) / kScanTile);
     vtx_tile_sum_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, n, tmp);
-    tile_excl_scan_kernel<<<1, kScanThreads, 0, st>>>(tmp, ntiles, nullptr);
-    vtx_tile_write_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, n, tmp, voff, cnt, cursor);
+    tile_excl_scan_kernel<<<1, kScanThreads, 0, st>>>(tmp, ntiles);
+    vtx_tile_write_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, n, tmp, voff, cnt, cnt2, cursor);
     return cudaGetLastError();
 }
 
 // ===========================================================================
-// Inverted index scatter: for every member u of set s in [set_begin,
-// set_end), inv[voff[u] + cursor[u]++] = s (one-pass counting sort by vertex).
+// Inverted index scatter over list-stored sets: for every member u of set s
+// in [set_begin, set_end), inv[voff[u] + cursor[u]++] = s (one-pass counting
+// sort by vertex; bitmap sets have empty lists and add nothing).
 // ===========================================================================
 __global__ void __launch_bounds__(256)
 index_scatter_kernel(uint64_t set_begin, uint64_t set_end, const uint64_t* off, const uint32_t* arena,

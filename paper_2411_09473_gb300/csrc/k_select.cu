@@ -4,9 +4,10 @@
 //   argmax        PARALLEL_REDUCTION (Sec. IV-A): max over vertices not yet
 //                 picked of key = (count << 32) | (2^32 - 1 - v), so ties go to
 //                 the lowest id; thread -> warp shuffle -> block -> atomicMax.
-//   cover         every set holding the pick (read from the inverted index
-//                 segments) that is not yet covered is marked covered and
-//                 appended to this round's list; its size is summed.
+//   cover         every set holding the pick that is not yet covered is
+//                 marked covered and appended to this round's list; its size
+//                 is summed.  List-stored sets are found through the inverted
+//                 index segments, bitmap-stored sets by one bit test each.
 //   decrement     Alg. 2's update: one atomic decrement per member of each
 //                 newly covered set ...
 //   rebuild       ... or, when those members outnumber the members of the
@@ -74,14 +75,19 @@ __device__ __forceinline__ void warp_apply_sets(const uint32_t* arena, uint64_t 
 }
 
 // Decrement when the newly covered sets hold fewer members than a recount
-// would read: vol_cov <= members still uncovered afterwards + n/8 + sets/8.
+// would read: vol_cov <= list members still uncovered afterwards + words/8 per
+// uncovered bitmap + n/8 + sets/8.
 __device__ int round_mode(const SelectState& s, uint32_t j)
 {
-    uint64_t before = 0;
-    for (uint32_t i = 0; i < j; ++i) before += s.vol_cov[i];
+    uint64_t before_list = 0, before_b = 0;
+    for (uint32_t i = 0; i < j; ++i) {
+        before_list += s.vol_list[i];
+        before_b += s.bmp_cov[i];
+    }
     const uint64_t cov = s.vol_cov[j];
-    const uint64_t unc_after = s.total_members - before - cov;
-    const uint64_t rebuild_cost = unc_after + (s.n >> 3) + (s.nsets >> 3);
+    const uint64_t unc_list = s.list_members - before_list - s.vol_list[j];
+    const uint64_t unc_bmp = (uint64_t)s.nbmp - before_b - s.bmp_cov[j];
+    const uint64_t rebuild_cost = unc_list + unc_bmp * (s.words >> 3) + (s.n >> 3) + (s.nsets >> 3);
     return cov > rebuild_cost ? kModeRebuild : kModeDecrement;
 }
 
@@ -127,7 +133,7 @@ cover_kernel(SelectState s, uint32_t j)
     }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long vol = 0;
+    unsigned long long vol = 0, nb = 0;
     for (uint32_t g = 0; g < s.nsegs; ++g) {
         const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
         const uint32_t* inv = s.segs[g].inv;
@@ -142,7 +148,24 @@ cover_kernel(SelectState s, uint32_t j)
             }
         }
     }
+    if (vol) {
+        atomicAdd(&s.vol_cov[j], vol);
+        atomicAdd(&s.vol_list[j], vol);
+    }
+    vol = 0;
+    const uint32_t wv = v >> 5, bit = 1u << (v & 31);
+    for (uint64_t b = tid; b < s.nbmp; b += stride) {
+        const uint32_t sid = s.bmp_set[b];
+        if (!s.covered[sid] && (s.bmp[b * s.words + wv] & bit)) {
+            s.covered[sid] = 1;
+            const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
+            s.newly[p] = sid;
+            vol += s.bmp_len[b];
+            ++nb;
+        }
+    }
     if (vol) atomicAdd(&s.vol_cov[j], vol);
+    if (nb) atomicAdd(&s.bmp_cov[j], nb);
 }
 
 __global__ void __launch_bounds__(256)
@@ -159,13 +182,30 @@ decrement_kernel(SelectState s, uint32_t j)
     for (uint64_t first = gw * 32; first < cnt; first += nw * 32) {
         const uint64_t i = first + lane;
         uint64_t start = 0;
-        uint32_t len = 0;
+        uint32_t len = 0, bid = kEmpty;
         if (i < cnt) {
             const uint32_t sid = s.newly[i];
             start = s.off[sid];
             len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+            bid = s.set_bmp[sid];
         }
         warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);  // += -1
+        // bitmap-stored sets: the warp walks the set bits of each one
+        uint32_t bm = __ballot_sync(kFull, bid != kEmpty);
+        while (bm) {
+            const int o = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const uint32_t B = __shfl_sync(kFull, bid, o);
+            const uint32_t* row = s.bmp + (uint64_t)B * s.words;
+            for (uint32_t w = lane; w < s.words; w += 32) {
+                uint32_t x = row[w];
+                while (x) {
+                    const int t = __ffs(x) - 1;
+                    x &= x - 1;
+                    atomicAdd(&s.work[w * 32 + t], 0xFFFFFFFFu);
+                }
+            }
+        }
     }
 }
 
@@ -202,6 +242,37 @@ rebuild_add_kernel(SelectState s, uint32_t j)
     }
 }
 
+// Rebuild, bitmap-stored part: counts of the uncovered bitmap sets added by
+// columns (each thread owns the 32 vertices of one bitmap word).
+__global__ void __launch_bounds__(256)
+rebuild_bitmap_kernel(SelectState s, uint32_t j, uint64_t per_chunk)
+{
+    __shared__ int s_mode;
+    if (threadIdx.x == 0) s_mode = round_mode(s, j);
+    __syncthreads();
+    if (s_mode != kModeRebuild) return;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t b0 = (uint64_t)blockIdx.y * per_chunk;
+    uint64_t b1 = b0 + per_chunk;
+    if (b1 > s.nbmp) b1 = s.nbmp;
+    if (w >= s.words) return;
+    uint32_t c[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) c[i] = 0;
+    for (uint64_t b = b0; b < b1; ++b) {
+        if (s.covered[s.bmp_set[b]]) continue;
+        const uint32_t x = __ldg(s.bmp + b * s.words + w);
+        if (!x) continue;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) c[i] += (x >> i) & 1u;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const uint32_t v = w * 32 + i;
+        if (c[i] && v < s.n) atomicAdd(&s.work[v], c[i]);
+    }
+}
+
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
                                 uint64_t* launches)
 {
@@ -218,7 +289,18 @@ cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceIn
     if (rb > sms * 8) rb = sms * 8;
     if (rb == 0) rb = 1;
     rebuild_add_kernel<<<(unsigned)rb, 256, 0, st>>>(s, j);
-    if (launches) *launches += 5;
+    int n = 5;
+    if (s.nbmp) {
+        const uint32_t bx = (s.words + 255) / 256;
+        uint64_t chunks = ((uint64_t)sms * 8 + bx - 1) / bx;
+        if (chunks > s.nbmp) chunks = s.nbmp;
+        if (chunks > 65535) chunks = 65535;
+        const uint64_t per = (s.nbmp + chunks - 1) / chunks;
+        chunks = (s.nbmp + per - 1) / per;
+        rebuild_bitmap_kernel<<<dim3(bx, (unsigned)chunks), 256, 0, st>>>(s, j, per);
+        ++n;
+    }
+    if (launches) *launches += n;
     return cudaGetLastError();
 }
 

@@ -93,7 +93,12 @@ def test_ic_rmat_giant_sets(imm, n, m, gseed, pmax):
     # high edge probabilities: many sets outgrow a warp and go to the CTA path
     g = graphgen.make_graph(n, m, gseed, IC, "uniform", pmax=pmax)
     ctx = new_ctx(imm, g)
-    check_stream(imm, ctx, g, 1500, gseed)
+    o = check_stream(imm, ctx, g, 1500, gseed)
+    # sets above n/32 members are stored as bitmaps: selection must see them
+    for k in (1, 5, 40):
+        seeds, cov = imm.imm_select(ctx, k)
+        want, wcov = o.select(k)
+        assert np.array_equal(seeds, want) and cov == wcov
 
 
 def test_ic_p1_closures_and_star_hub(imm):
