@@ -306,18 +306,41 @@ __device__ __forceinline__ void visit_live(uint32_t live, uint32_t quad, const u
     }
 }
 
+// Two quads of one vertex per lane: loads and Philox chains of both are
+// issued before either live mask is consumed.
+__device__ __forceinline__ void expand_two(uint32_t qa, bool ha, uint32_t qb, bool hb, uint32_t rs, uint32_t re,
+                                           uint32_t s_lo, uint32_t s_hi, uint2 key, const DevGraph& g,
+                                           uint32_t* bm, uint32_t* q, uint32_t* s_tail)
+{
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    const uint4 tha = ha ? load_thr4(g.thr, qa) : z;
+    const uint4 thb = hb ? load_thr4(g.thr, qb) : z;
+    const uint4 wa = philox(make_uint4(s_lo, s_hi, qa, kTagIC), key);
+    const uint4 wb = philox(make_uint4(s_lo, s_hi, qb, kTagIC), key);
+    const uint32_t la = ha ? live_mask(wa, tha, qa, rs, re) : 0u;
+    const uint32_t lb = hb ? live_mask(wb, thb, qb, rs, re) : 0u;
+    visit_live(la, qa, g.src, bm, q, s_tail);
+    visit_live(lb, qb, g.src, bm, q, s_tail);
+}
+
+constexpr uint32_t kHeavyQuads = 64;    // vertices with this many in-edge quads are split
+constexpr uint32_t kHeavyCap = 1024;    // heavy vertices listed per level (more: swept in place)
+
 template <bool kSmemBitmap>
 __global__ void __launch_bounds__(kLargeThreads, 1)
 ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
 {
     extern __shared__ __align__(16) uint32_t dyn_bitmap[];
-    __shared__ uint32_t s_tail, s_next, s_end, s_claim;
+    __shared__ uint32_t s_hrs[kHeavyCap], s_hre[kHeavyCap], s_hpre[kHeavyCap + 1];
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_tail, s_next, s_end, s_claim, s_nheavy, s_hnext;
     __shared__ int s_ok;
     __shared__ unsigned long long s_pos;
     __shared__ unsigned long long s_edges;
 
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31;
+    const int wid = tid >> 5;
     const uint32_t words = b.words;
     uint32_t* bm = kSmemBitmap ? dyn_bitmap : ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
@@ -345,13 +368,16 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
             s_tail = 1;
             s_next = 0;
             s_end = 1;
+            s_nheavy = 0;
+            s_hnext = 0;
         }
         __syncthreads();
 
         uint32_t edges = 0;
         uint32_t end = s_end;
         for (;;) {
-            // one level: warps claim 32-vertex chunks of q[.. end)
+            // ---- level q[.. end): warps claim 32-vertex chunks; light
+            // vertices are expanded at once, heavy ones are listed
             for (;;) {
                 uint32_t c = 0;
                 if (lane == 0) c = atomicAdd(&s_next, 32u);
@@ -364,29 +390,27 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                     nq = quads_of(rs, re);
                     edges += re - rs;
                 }
-                // vertices with >= 32 quads: the whole warp sweeps their quads
-                uint32_t bigm = __ballot_sync(kFull, nq >= 32);
+                if (nq >= kHeavyQuads) {
+                    const uint32_t hp = atomicAdd(&s_nheavy, 1u);
+                    if (hp < kHeavyCap) {
+                        s_hrs[hp] = rs;
+                        s_hre[hp] = re;
+                        nq = 0;
+                    }
+                }
+                // leftovers when the heavy list is full: swept by this warp
+                uint32_t bigm = __ballot_sync(kFull, nq >= kHeavyQuads);
                 while (bigm) {
                     const int o = __ffs(bigm) - 1;
                     bigm &= bigm - 1;
                     const uint32_t ors = __shfl_sync(kFull, rs, o);
                     const uint32_t ore = __shfl_sync(kFull, re, o);
                     const uint32_t q1 = (ore - 1) >> 2;
-                    for (uint32_t qa = (ors >> 2) + lane; qa <= q1; qa += 64) {
-                        const uint32_t qb = qa + 32;
-                        const bool hb = qb <= q1;
-                        const uint4 tha = load_thr4(g.thr, qa);
-                        const uint4 thb = hb ? load_thr4(g.thr, qb) : make_uint4(0, 0, 0, 0);
-                        const uint4 wa = philox(make_uint4(s_lo, s_hi, qa, kTagIC), key);
-                        const uint4 wb = philox(make_uint4(s_lo, s_hi, qb, kTagIC), key);
-                        const uint32_t la = live_mask(wa, tha, qa, ors, ore);
-                        const uint32_t lb = hb ? live_mask(wb, thb, qb, ors, ore) : 0u;
-                        visit_live(la, qa, g.src, bm, q, &s_tail);
-                        visit_live(lb, qb, g.src, bm, q, &s_tail);
-                    }
+                    for (uint32_t qa = (ors >> 2) + lane; qa <= q1; qa += 64)
+                        expand_two(qa, true, qa + 32, qa + 32 <= q1, ors, ore, s_lo, s_hi, key, g, bm, q, &s_tail);
                 }
-                // the rest: flattened across lanes
-                const uint32_t sq = nq >= 32 ? 0u : nq;
+                // light vertices: quads flattened across lanes, two per lane
+                const uint32_t sq = nq >= kHeavyQuads ? 0u : nq;
                 uint32_t incl = sq;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
@@ -395,29 +419,81 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                 }
                 const uint32_t total = __shfl_sync(kFull, incl, 31);
                 const uint32_t excl = incl - sq;
-                for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-                    const uint32_t j = j0 + lane;
-                    uint32_t o = 0;
+                for (uint32_t j0 = 0; j0 < total; j0 += 64) {
+                    const uint32_t ja = j0 + lane, jb = ja + 32;
+                    uint32_t oa = 0, ob = 0;
 #pragma unroll
                     for (int step = 16; step > 0; step >>= 1) {
-                        const uint32_t cc = __shfl_sync(kFull, incl, o + step - 1);
-                        if (cc <= j) o += step;
+                        const uint32_t ca = __shfl_sync(kFull, incl, oa + step - 1);
+                        const uint32_t cb = __shfl_sync(kFull, incl, ob + step - 1);
+                        if (ca <= ja) oa += step;
+                        if (cb <= jb) ob += step;
                     }
-                    const uint32_t ors = __shfl_sync(kFull, rs, o);
-                    const uint32_t ore = __shfl_sync(kFull, re, o);
-                    const uint32_t oex = __shfl_sync(kFull, excl, o);
-                    if (j < total) {
-                        const uint32_t quad = (ors >> 2) + (j - oex);
-                        const uint4 th = load_thr4(g.thr, quad);
-                        const uint4 w = philox(make_uint4(s_lo, s_hi, quad, kTagIC), key);
-                        visit_live(live_mask(w, th, quad, ors, ore), quad, g.src, bm, q, &s_tail);
+                    const uint32_t rsa = __shfl_sync(kFull, rs, oa), rea = __shfl_sync(kFull, re, oa);
+                    const uint32_t rsb = __shfl_sync(kFull, rs, ob), reb = __shfl_sync(kFull, re, ob);
+                    const uint32_t exa = __shfl_sync(kFull, excl, oa), exb = __shfl_sync(kFull, excl, ob);
+                    const bool ha = ja < total, hb = jb < total;
+                    const uint32_t qa = (rsa >> 2) + (ja - exa);
+                    const uint32_t qb = (rsb >> 2) + (jb - exb);
+                    if (rsa == rsb) {
+                        expand_two(qa, ha, qb, hb, rsa, rea, s_lo, s_hi, key, g, bm, q, &s_tail);
+                    } else {
+                        expand_two(qa, ha, qa, false, rsa, rea, s_lo, s_hi, key, g, bm, q, &s_tail);
+                        expand_two(qb, hb, qb, false, rsb, reb, s_lo, s_hi, key, g, bm, q, &s_tail);
                     }
+                }
+            }
+            __syncthreads();
+            // ---- heavy vertices of the level: 64-quad chunks shared by all warps
+            const uint32_t nh = min(s_nheavy, kHeavyCap);
+            if (nh) {
+                const uint32_t ch = tid < nh ? (quads_of(s_hrs[tid], s_hre[tid]) + 63) / 64 : 0u;
+                uint32_t incl = ch;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, incl, d);
+                    if (lane >= d) incl += t;
+                }
+                if (lane == 31) s_warp[wid] = incl;
+                __syncthreads();
+                if (wid == 0) {
+                    uint32_t x = s_warp[lane];
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t t = __shfl_up_sync(kFull, x, d);
+                        if (lane >= d) x += t;
+                    }
+                    s_warp[lane] = x;
+                }
+                __syncthreads();
+                const uint32_t inclb = incl + (wid ? s_warp[wid - 1] : 0u);
+                if (tid < nh) s_hpre[tid] = inclb - ch;
+                if (tid == 0) s_hpre[nh] = s_warp[31];
+                __syncthreads();
+                const uint32_t nchunks = s_hpre[nh];
+                for (;;) {
+                    uint32_t c = 0;
+                    if (lane == 0) c = atomicAdd(&s_hnext, 1u);
+                    c = __shfl_sync(kFull, c, 0);
+                    if (c >= nchunks) break;
+                    uint32_t lo = 0, hi = nh;  // s_hpre[lo] <= c < s_hpre[hi]
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (s_hpre[mid] <= c) lo = mid;
+                        else hi = mid;
+                    }
+                    const uint32_t hrs = s_hrs[lo], hre = s_hre[lo];
+                    const uint32_t q1 = (hre - 1) >> 2;
+                    const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * 64 + lane;
+                    expand_two(qa, qa <= q1, qa + 32, qa + 32 <= q1, hrs, hre, s_lo, s_hi, key, g, bm, q, &s_tail);
                 }
             }
             __syncthreads();
             if (tid == 0) {
                 s_next = end;
                 s_end = s_tail;
+                s_nheavy = 0;
+                s_hnext = 0;
             }
             __syncthreads();
             const uint32_t ne = s_end;
@@ -465,7 +541,8 @@ static size_t large_smem_bytes(uint32_t n)
 
 int ic_large_uses_smem(uint32_t n, const DeviceInfo& di)
 {
-    return large_smem_bytes(n) + 4096 <= (size_t)di.max_smem_optin;
+    // static shared memory of the kernel: 3 x kHeavyCap words + small scalars
+    return large_smem_bytes(n) + 3 * kHeavyCap * 4 + 1024 <= (size_t)di.max_smem_optin;
 }
 
 cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls, const DeviceInfo& di,
