@@ -324,14 +324,21 @@ __device__ __forceinline__ void expand_two(uint32_t qa, bool ha, uint32_t qb, bo
 }
 
 constexpr uint32_t kHeavyQuads = 64;    // vertices with this many in-edge quads are split
-constexpr uint32_t kHeavyCap = 1024;    // heavy vertices listed per level (more: swept in place)
+constexpr uint32_t kHeavyMax = 8192;    // heavy vertices listed per level (more: swept in place)
+
+// Dynamic shared memory of the large path: [bitmap words (when it fits)]
+// [heavy vertex ids: hcap][heavy chunk prefix: hcap + 1].
+__host__ __device__ __forceinline__ size_t bitmap_smem_bytes(uint32_t n)
+{
+    const uint64_t words = ((uint64_t)n + 31) >> 5;
+    return (size_t)(((words * 4) + 15) / 16 * 16);
+}
 
 template <bool kSmemBitmap>
 __global__ void __launch_bounds__(kLargeThreads, 1)
-ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
+ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
 {
-    extern __shared__ __align__(16) uint32_t dyn_bitmap[];
-    __shared__ uint32_t s_hrs[kHeavyCap], s_hre[kHeavyCap], s_hpre[kHeavyCap + 1];
+    extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_tail, s_next, s_end, s_claim, s_nheavy, s_hnext;
     __shared__ int s_ok;
@@ -342,7 +349,10 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
     const int lane = tid & 31;
     const int wid = tid >> 5;
     const uint32_t words = b.words;
-    uint32_t* bm = kSmemBitmap ? dyn_bitmap : ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
+    const uint32_t bm_words = kSmemBitmap ? (uint32_t)(bitmap_smem_bytes(g.n) / 4) : 0u;
+    uint32_t* bm = kSmemBitmap ? dyn : ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
+    uint32_t* s_hv = dyn + bm_words;
+    uint32_t* s_hpre = s_hv + hcap;
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
     const uint2 key = philox_key(b.seed);
     const uint32_t large_count = b.sc->large_count;  // final: written by the previous launch
@@ -384,17 +394,17 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                 c = __shfl_sync(kFull, c, 0);
                 if (c >= end) break;
                 const uint32_t nf = min(end - c, 32u);
-                uint32_t rs = 0, re = 0, nq = 0;
+                uint32_t v = 0, rs = 0, re = 0, nq = 0;
                 if ((uint32_t)lane < nf) {
-                    edge_range(g, q[c + lane], rs, re);
+                    v = q[c + lane];
+                    edge_range(g, v, rs, re);
                     nq = quads_of(rs, re);
                     edges += re - rs;
                 }
                 if (nq >= kHeavyQuads) {
                     const uint32_t hp = atomicAdd(&s_nheavy, 1u);
-                    if (hp < kHeavyCap) {
-                        s_hrs[hp] = rs;
-                        s_hre[hp] = re;
+                    if (hp < hcap) {
+                        s_hv[hp] = v;
                         nq = 0;
                     }
                 }
@@ -445,10 +455,18 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
             }
             __syncthreads();
             // ---- heavy vertices of the level: 64-quad chunks shared by all warps
-            const uint32_t nh = min(s_nheavy, kHeavyCap);
+            const uint32_t nh = min(s_nheavy, hcap);
             if (nh) {
-                const uint32_t ch = tid < nh ? (quads_of(s_hrs[tid], s_hre[tid]) + 63) / 64 : 0u;
-                uint32_t incl = ch;
+                // block-wide exclusive scan of the chunk counts (hcap / 1024 per thread)
+                const uint32_t per = (nh + kLargeThreads - 1) / kLargeThreads;
+                const uint32_t i0 = tid * per;
+                uint32_t local = 0;
+                for (uint32_t i = i0; i < i0 + per && i < nh; ++i) {
+                    uint32_t hrs, hre;
+                    edge_range(g, s_hv[i], hrs, hre);
+                    local += (quads_of(hrs, hre) + kHeavyQuads - 1) / kHeavyQuads;
+                }
+                uint32_t incl = local;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const uint32_t t = __shfl_up_sync(kFull, incl, d);
@@ -466,8 +484,13 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                     s_warp[lane] = x;
                 }
                 __syncthreads();
-                const uint32_t inclb = incl + (wid ? s_warp[wid - 1] : 0u);
-                if (tid < nh) s_hpre[tid] = inclb - ch;
+                uint32_t run = incl - local + (wid ? s_warp[wid - 1] : 0u);
+                for (uint32_t i = i0; i < i0 + per && i < nh; ++i) {
+                    s_hpre[i] = run;
+                    uint32_t hrs, hre;
+                    edge_range(g, s_hv[i], hrs, hre);
+                    run += (quads_of(hrs, hre) + kHeavyQuads - 1) / kHeavyQuads;
+                }
                 if (tid == 0) s_hpre[nh] = s_warp[31];
                 __syncthreads();
                 const uint32_t nchunks = s_hpre[nh];
@@ -482,9 +505,10 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                         if (s_hpre[mid] <= c) lo = mid;
                         else hi = mid;
                     }
-                    const uint32_t hrs = s_hrs[lo], hre = s_hre[lo];
+                    uint32_t hrs, hre;
+                    edge_range(g, s_hv[lo], hrs, hre);
                     const uint32_t q1 = (hre - 1) >> 2;
-                    const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * 64 + lane;
+                    const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * kHeavyQuads + lane;
                     expand_two(qa, qa <= q1, qa + 32, qa + 32 <= q1, hrs, hre, s_lo, s_hi, key, g, bm, q, &s_tail);
                 }
             }
@@ -535,28 +559,42 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
 
 static size_t large_smem_bytes(uint32_t n)
 {
-    const uint64_t words = ((uint64_t)n + 31) >> 5;
-    return (size_t)(((words * 4) + 15) / 16 * 16);
+    return bitmap_smem_bytes(n);
 }
 
 int ic_large_uses_smem(uint32_t n, const DeviceInfo& di)
 {
-    // static shared memory of the kernel: 3 x kHeavyCap words + small scalars
-    return large_smem_bytes(n) + 3 * kHeavyCap * 4 + 1024 <= (size_t)di.max_smem_optin;
+    // the bitmap plus a heavy-vertex list of at least 1024 entries
+    return large_smem_bytes(n) + 8 * 1024 + 1024 <= (size_t)di.max_smem_optin;
+}
+
+// heavy-list capacity that fits beside the bitmap (or alone)
+static uint32_t heavy_cap(uint32_t n, bool smem_bitmap, const DeviceInfo& di)
+{
+    const size_t used = (smem_bitmap ? large_smem_bytes(n) : 0) + 1024;
+    const size_t room = (size_t)di.max_smem_optin > used ? (size_t)di.max_smem_optin - used : 0;
+    size_t cap = room / 8;
+    if (cap > kHeavyMax) cap = kHeavyMax;
+    return (uint32_t)(cap > 16 ? cap - 1 : 0);
 }
 
 cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls, const DeviceInfo& di,
                             cudaStream_t st)
 {
     const unsigned grid = ls.nslots;
-    if (ic_large_uses_smem(g.n, di)) {
-        const size_t smem = large_smem_bytes(g.n);
+    const bool smem_bm = ic_large_uses_smem(g.n, di) != 0;
+    const uint32_t hcap = heavy_cap(g.n, smem_bm, di);
+    const size_t smem = (smem_bm ? large_smem_bytes(g.n) : 0) + (size_t)(2 * hcap + 1) * 4;
+    if (smem_bm) {
         cudaError_t e = cudaFuncSetAttribute(ic_large_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        ic_large_kernel<true><<<grid, kLargeThreads, smem, st>>>(g, b, ls);
+        ic_large_kernel<true><<<grid, kLargeThreads, smem, st>>>(g, b, ls, hcap);
     } else {
-        ic_large_kernel<false><<<grid, kLargeThreads, 0, st>>>(g, b, ls);
+        cudaError_t e = cudaFuncSetAttribute(ic_large_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        ic_large_kernel<false><<<grid, kLargeThreads, smem, st>>>(g, b, ls, hcap);
     }
     return cudaGetLastError();
 }
