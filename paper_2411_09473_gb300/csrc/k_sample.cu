@@ -306,21 +306,40 @@ __device__ __forceinline__ void visit_live(uint32_t live, uint32_t quad, const u
     }
 }
 
-// Two quads of one vertex per lane: loads and Philox chains of both are
-// issued before either live mask is consumed.
-__device__ __forceinline__ void expand_two(uint32_t qa, bool ha, uint32_t qb, bool hb, uint32_t rs, uint32_t re,
-                                           uint32_t s_lo, uint32_t s_hi, uint2 key, const DevGraph& g,
-                                           uint32_t* bm, uint32_t* q, uint32_t* s_tail)
+constexpr uint32_t kWarpBuf = 128;
+__device__ __forceinline__ void expand_pair(uint32_t qa, bool ha, uint32_t rsa, uint32_t rea, uint32_t qb, bool hb,
+                                            uint32_t rsb, uint32_t reb, uint32_t s_lo, uint32_t s_hi, uint2 key,
+                                            const DevGraph& g, uint32_t* bm, uint32_t* q, uint32_t* s_tail,
+                                            uint32_t* wbuf)
 {
-    const uint4 z = make_uint4(0, 0, 0, 0);
-    const uint4 tha = ha ? load_thr4(g.thr, qa) : z;
-    const uint4 thb = hb ? load_thr4(g.thr, qb) : z;
-    const uint4 wa = philox(make_uint4(s_lo, s_hi, qa, kTagIC), key);
-    const uint4 wb = philox(make_uint4(s_lo, s_hi, qb, kTagIC), key);
-    const uint32_t la = ha ? live_mask(wa, tha, qa, rs, re) : 0u;
-    const uint32_t lb = hb ? live_mask(wb, thb, qb, rs, re) : 0u;
-    visit_live(la, qa, g.src, bm, q, s_tail);
-    visit_live(lb, qb, g.src, bm, q, s_tail);
+    uint4 tha = make_uint4(0, 0, 0, 0), thb = tha, wa = tha, wb = tha;
+    if (ha) tha = load_thr4(g.thr, qa);
+    if (hb) thb = load_thr4(g.thr, qb);
+    if (ha) wa = philox(make_uint4(s_lo, s_hi, qa, kTagIC), key);
+    if (hb) wb = philox(make_uint4(s_lo, s_hi, qb, kTagIC), key);
+    uint32_t la = ha ? live_mask(wa, tha, qa, rsa, rea) : 0u;
+    uint32_t lb = hb ? live_mask(wb, thb, qb, rsb, reb) : 0u;
+    const int lane = threadIdx.x & 31;
+    const uint32_t cnt = __popc(la) + __popc(lb);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    if (total > kWarpBuf) {
+        visit_live(la, qa, g.src, bm, q, s_tail);
+        visit_live(lb, qb, g.src, bm, q, s_tail);
+        return;
+    }
+    uint32_t p = incl - cnt;
+    while (la) { const int t = __ffs(la) - 1; la &= la - 1; wbuf[p++] = (qa << 2) + t; }
+    while (lb) { const int t = __ffs(lb) - 1; lb &= lb - 1; wbuf[p++] = (qb << 2) + t; }
+    __syncwarp();
+    for (uint32_t i = lane; i < total; i += 32) visit(__ldg(g.src + wbuf[i]), bm, q, s_tail);
+    __syncwarp();
 }
 
 constexpr uint32_t kHeavyQuads = 64;    // vertices with this many in-edge quads are split
@@ -340,6 +359,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
 {
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_wbuf[32][kWarpBuf];
     __shared__ uint32_t s_tail, s_next, s_end, s_claim, s_nheavy, s_hnext;
     __shared__ int s_ok;
     __shared__ unsigned long long s_pos;
@@ -348,6 +368,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31;
     const int wid = tid >> 5;
+    uint32_t* wbuf = s_wbuf[wid];
     const uint32_t words = b.words;
     const uint32_t bm_words = kSmemBitmap ? (uint32_t)(bitmap_smem_bytes(g.n) / 4) : 0u;
     uint32_t* bm = kSmemBitmap ? dyn : ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
@@ -416,8 +437,11 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     const uint32_t ors = __shfl_sync(kFull, rs, o);
                     const uint32_t ore = __shfl_sync(kFull, re, o);
                     const uint32_t q1 = (ore - 1) >> 2;
-                    for (uint32_t qa = (ors >> 2) + lane; qa <= q1; qa += 64)
-                        expand_two(qa, true, qa + 32, qa + 32 <= q1, ors, ore, s_lo, s_hi, key, g, bm, q, &s_tail);
+                    for (uint32_t q0 = (ors >> 2); q0 <= q1; q0 += 64) {
+                        const uint32_t qa = q0 + lane;
+                        expand_pair(qa, qa <= q1, ors, ore, qa + 32, qa + 32 <= q1, ors, ore, s_lo, s_hi, key, g, bm,
+                                    q, &s_tail, wbuf);
+                    }
                 }
                 // light vertices: quads flattened across lanes, two per lane
                 const uint32_t sq = nq >= kHeavyQuads ? 0u : nq;
@@ -445,12 +469,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     const bool ha = ja < total, hb = jb < total;
                     const uint32_t qa = (rsa >> 2) + (ja - exa);
                     const uint32_t qb = (rsb >> 2) + (jb - exb);
-                    if (rsa == rsb) {
-                        expand_two(qa, ha, qb, hb, rsa, rea, s_lo, s_hi, key, g, bm, q, &s_tail);
-                    } else {
-                        expand_two(qa, ha, qa, false, rsa, rea, s_lo, s_hi, key, g, bm, q, &s_tail);
-                        expand_two(qb, hb, qb, false, rsb, reb, s_lo, s_hi, key, g, bm, q, &s_tail);
-                    }
+                    expand_pair(qa, ha, rsa, rea, qb, hb, rsb, reb, s_lo, s_hi, key, g, bm, q, &s_tail, wbuf);
                 }
             }
             __syncthreads();
@@ -509,7 +528,8 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     edge_range(g, s_hv[lo], hrs, hre);
                     const uint32_t q1 = (hre - 1) >> 2;
                     const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * kHeavyQuads + lane;
-                    expand_two(qa, qa <= q1, qa + 32, qa + 32 <= q1, hrs, hre, s_lo, s_hi, key, g, bm, q, &s_tail);
+                    expand_pair(qa, qa <= q1, hrs, hre, qa + 32, qa + 32 <= q1, hrs, hre, s_lo, s_hi, key, g, bm, q,
+                                &s_tail, wbuf);
                 }
             }
             __syncthreads();
@@ -571,7 +591,7 @@ int ic_large_uses_smem(uint32_t n, const DeviceInfo& di)
 // heavy-list capacity that fits beside the bitmap (or alone)
 static uint32_t heavy_cap(uint32_t n, bool smem_bitmap, const DeviceInfo& di)
 {
-    const size_t used = (smem_bitmap ? large_smem_bytes(n) : 0) + 1024;
+    const size_t used = (smem_bitmap ? large_smem_bytes(n) : 0) + 1024 + 32 * kWarpBuf * 4;
     const size_t room = (size_t)di.max_smem_optin > used ? (size_t)di.max_smem_optin - used : 0;
     size_t cap = room / 8;
     if (cap > kHeavyMax) cap = kHeavyMax;
