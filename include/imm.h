@@ -187,6 +187,39 @@ int imm_get_counts(imm_ctx* ctx, uint32_t* cnt_out);
  * (0 = unlimited).  imm_sample returns ENOMEM instead of growing past it. */
 int imm_set_arena_limit(imm_ctx* ctx, uint64_t bytes);
 
+/* ---- selection without device allocation ----
+ * No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory at run time, for example a plugin inside
+ * another framework whose memory pool owns the whole GPU, or a service whose
+ * memory footprint is fixed when it starts.
+ *
+ * Same greedy max coverage as imm_select (Alg. 2: k rounds, ties to the
+ * lowest vertex id, picked vertices excluded, picking continues at count 0),
+ * over a set system the caller already holds on the device:
+ *   d_off      device uint64[nsets + 1], member offsets (nondecreasing, d_off[0] = 0)
+ *   d_members  device uint32[d_off[nsets]], vertex ids < n, distinct within a set
+ *   d_seeds_out   device uint32[k]: the picks in order
+ *   d_covered_out device uint64 (nullable): number of sets covered
+ *   stream     cudaStream_t (NULL = legacy default stream); the call is
+ *              asynchronous on it and returns once the work is enqueued.
+ * It allocates and frees nothing (no cudaMalloc/cudaFree, no allocating
+ * library routine).  Its scratch is one fixed array compiled into the library
+ * (about 9 MB), held on every GPU that loads the library until the process
+ * exits.  Limits: n <= IMM_NOALLOC_MAX_N, nsets <= IMM_NOALLOC_MAX_SETS,
+ * k <= IMM_NOALLOC_MAX_K.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and clears what must start at zero; calls that
+ * overlap on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller.
+ * Errors: EINVAL (n == 0, k == 0, k > n, a size above its limit, a NULL
+ * required pointer), ECUDA (device lookup or launch failed). */
+#define IMM_NOALLOC_MAX_N    (1u << 20)
+#define IMM_NOALLOC_MAX_SETS (1u << 22)
+#define IMM_NOALLOC_MAX_K    4096u
+int imm_select_noalloc(uint32_t n, uint64_t nsets, const uint64_t* d_off, const uint32_t* d_members,
+                       uint32_t k, uint32_t* d_seeds_out, unsigned long long* d_covered_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,7 @@ def _load():
         "imm_get_sets": ([vp, u64, u64, vp, vp, u64], i32),
         "imm_get_counts": ([vp, vp], i32),
         "imm_set_arena_limit": ([vp, u64], i32),
+        "imm_select_noalloc": ([u32, u64, vp, vp, u32, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -254,3 +255,28 @@ def imm_get_counts(ctx: _Ctx, n: int) -> np.ndarray:
 
 def imm_set_arena_limit(ctx: _Ctx, nbytes: int) -> None:
     _check(ctx, _load().imm_set_arena_limit(ctx.handle, nbytes))
+
+
+IMM_NOALLOC_MAX_N = 1 << 20
+IMM_NOALLOC_MAX_SETS = 1 << 22
+IMM_NOALLOC_MAX_K = 4096
+
+
+def imm_select_noalloc(n: int, nsets: int, d_off, d_members, k: int, d_seeds_out, d_covered_out=None,
+                       stream=None) -> None:
+    """Greedy selection over a device-resident set system without any device
+    allocation (for callers that cannot allocate).  d_off: CUDA int64 tensor
+    [nsets+1]; d_members: CUDA int32 tensor; d_seeds_out: CUDA int32 tensor [k];
+    d_covered_out: CUDA int64 tensor [1] or None.  Enqueued on `stream`
+    (default: torch's current stream); raises ImmError on a rejected call."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    mem_ptr = d_members.data_ptr() if d_members is not None and d_members.numel() else None
+    cov_ptr = d_covered_out.data_ptr() if d_covered_out is not None else None
+    rc = _load().imm_select_noalloc(n, nsets, d_off.data_ptr(), mem_ptr, k, d_seeds_out.data_ptr(), cov_ptr,
+                                     ctypes.c_void_p(st))
+    if rc != IMM_OK:
+        raise ImmError(rc, "imm_select_noalloc rejected the call (sizes above the fixed scratch limits, "
+                           "bad k, or a NULL pointer)" if rc == IMM_EINVAL else "CUDA error")
