@@ -48,6 +48,11 @@ def main():
         torch.cuda.synchronize()
         rec["s"] = time.perf_counter() - t0
         rec["sets"], rec["members"] = imm.imm_stream_size(ctx)
+        # in-edges examined = sum over members of their in-degree
+        import numpy as np
+        cnt = imm.imm_get_counts(ctx, g.n).astype(np.uint64)
+        indeg = np.diff(g.row.astype(np.int64)).astype(np.uint64)
+        rec["edges"] = int((cnt * indeg).sum())
         out.append(rec)
     print(json.dumps(out))
     imm.imm_destroy(ctx)
