@@ -343,6 +343,7 @@ __device__ __forceinline__ void expand_pair(uint32_t qa, bool ha, uint32_t rsa, 
 }
 
 constexpr uint32_t kHeavyQuads = 64;    // vertices with this many in-edge quads are split
+constexpr uint32_t kChunkQuads = 64;    // quads of a heavy vertex per claimed chunk (2 per lane)
 constexpr uint32_t kHeavyMax = 8192;    // heavy vertices listed per level (more: swept in place)
 
 // Dynamic shared memory of the large path: [bitmap words (when it fits)]
@@ -483,7 +484,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                 for (uint32_t i = i0; i < i0 + per && i < nh; ++i) {
                     uint32_t hrs, hre;
                     edge_range(g, s_hv[i], hrs, hre);
-                    local += (quads_of(hrs, hre) + kHeavyQuads - 1) / kHeavyQuads;
+                    local += (quads_of(hrs, hre) + kChunkQuads - 1) / kChunkQuads;
                 }
                 uint32_t incl = local;
 #pragma unroll
@@ -508,7 +509,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     s_hpre[i] = run;
                     uint32_t hrs, hre;
                     edge_range(g, s_hv[i], hrs, hre);
-                    run += (quads_of(hrs, hre) + kHeavyQuads - 1) / kHeavyQuads;
+                    run += (quads_of(hrs, hre) + kChunkQuads - 1) / kChunkQuads;
                 }
                 if (tid == 0) s_hpre[nh] = s_warp[31];
                 __syncthreads();
@@ -527,7 +528,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     uint32_t hrs, hre;
                     edge_range(g, s_hv[lo], hrs, hre);
                     const uint32_t q1 = (hre - 1) >> 2;
-                    const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * kHeavyQuads + lane;
+                    const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * kChunkQuads + lane;
                     expand_pair(qa, qa <= q1, hrs, hre, qa + 32, qa + 32 <= q1, hrs, hre, s_lo, s_hi, key, g, bm, q,
                                 &s_tail, wbuf);
                 }
