@@ -31,6 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IMM seconds-to-seeds"
+
+# DRAM bytes per examined in-edge of ic_large_kernel, from one ncu capture of
+# the current kernel on the first 2,000 sets of the 1M-vertex IC workload
+# (profiles/ic_large_kernel__ic_u01_1m_first2000sets.md: 12.454 GB over
+# 4,620,412,076 in-edges).  Traffic of a full launch is scaled by its in-edges.
+IC_LARGE_DRAM_BYTES_PER_EDGE = 12.454e9 / 4620412076
 WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k")
 
 
@@ -352,10 +358,15 @@ def run_gpu(args, dist: Dist):
             "imm": {"theta": st.theta, "num_sets": st.num_sets, "members": st.members, "rounds": st.rounds,
                     "lb": st.lb, "covered": st.covered, "ms_sample": st.ms_sample, "ms_index": st.ms_index,
                     "ms_select": st.ms_select, "seeds_head": [int(x) for x in seeds[:10]]},
-            "roofline": {"kernel": "ic_small_kernel + ic_large_kernel (RRR sampling)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": None,
+            "roofline": {"kernel": "RRR sampling: ic_large_kernel (98.8% of device time) + ic_small_kernel",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": (IC_LARGE_DRAM_BYTES_PER_EDGE * edges / max(launches, 1)
+                                     if args.workload == "ic_u01_1m" else None),
+                         "traffic_source": ("ncu dram__bytes_read+write per in-edge of ic_large_kernel, scaled "
+                                            "to the average timed launch" if args.workload == "ic_u01_1m" else None),
                          "algorithmic_bytes": "8 B per examined in-edge + 16 B per member",
+                         "algorithmic_bytes_per_launch": algo_bytes / max(launches, 1),
                          "launches": launches},
             "gpu_launches": int(sum(s.kernel_launches for s in stats)),
             "clocks": clk,
