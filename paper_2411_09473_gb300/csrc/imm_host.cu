@@ -632,7 +632,16 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
-    for (uint32_t j = 0; j < k; ++j) CK(launch_select_round(s, j, c->di, c->stream, &c->acc_launches));
+    // all k rounds in one cooperative launch; per-round launches if the
+    // device refuses a cooperative grid of that size
+    const cudaError_t ce = launch_select_all(s, k, c->di, c->stream);
+    if (ce == cudaErrorCooperativeLaunchTooLarge || ce == cudaErrorNotSupported) {
+        cudaGetLastError();
+        for (uint32_t j = 0; j < k; ++j) CK(launch_select_round(s, j, c->di, c->stream, &c->acc_launches));
+    } else {
+        CK(ce);
+        c->acc_launches += 1;
+    }
     CK(cudaEventRecord(c->ev[1], c->stream));
     std::vector<unsigned long long> nn(k);
     CK(cudaMemcpyAsync(seeds_out, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, c->stream));

@@ -204,5 +204,11 @@ struct SelectState {
 };
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
                                 uint64_t* launches);
+// all k rounds in one cooperative launch over the whole GPU (one instance)
+cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st);
+// all k rounds of many instances in one launch, one CTA per instance
+// (states and ks in device memory)
+cudaError_t launch_select_batch(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,
+                                const DeviceInfo& di, cudaStream_t st);
 
 }  // namespace imm

@@ -15,6 +15,8 @@
 //                 uncovered sets (Sec. IV-C adaptive counter update).
 // The decrement/rebuild choice is taken on the device from the round's
 // volumes, so no host round trip is needed; both give the same counts.
+#include <cooperative_groups.h>
+
 #include "imm_internal.cuh"
 
 namespace imm {
@@ -271,6 +273,225 @@ rebuild_bitmap_kernel(SelectState s, uint32_t j, uint64_t per_chunk)
         const uint32_t v = w * 32 + i;
         if (c[i] && v < s.n) atomicAdd(&s.work[v], c[i]);
     }
+}
+
+// ===========================================================================
+// Persistent selection: all k rounds in one launch.  The phases above become
+// device functions run by a "team": the whole cooperative grid (one
+// instance, imm_select) or one CTA (many instances per launch, batches).
+// ===========================================================================
+namespace cg = cooperative_groups;
+
+struct GridTeam {
+    __device__ __forceinline__ uint64_t rank() const { return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ uint64_t size() const { return (uint64_t)gridDim.x * blockDim.x; }
+    __device__ __forceinline__ void sync() const { cg::this_grid().sync(); }
+};
+
+struct BlockTeam {
+    __device__ __forceinline__ uint64_t rank() const { return threadIdx.x; }
+    __device__ __forceinline__ uint64_t size() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+template <class Team>
+__device__ void team_argmax(const SelectState& s, uint32_t j, Team t)
+{
+    unsigned long long best = 0;
+    for (uint64_t v = t.rank(); v < s.n; v += t.size()) {
+        if (!s.picked[v]) {
+            const unsigned long long key = ((unsigned long long)s.work[v] << 32) | (0xFFFFFFFFu - (uint32_t)v);
+            best = key > best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+        best = o > best ? o : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&s.keys[j], best);
+}
+
+template <class Team>
+__device__ void team_cover(const SelectState& s, uint32_t j, Team t)
+{
+    const unsigned long long key = s.keys[j];
+    const uint32_t v = 0xFFFFFFFFu - (uint32_t)key;
+    if (t.rank() == 0) {
+        s.picked[v] = 1;
+        s.seeds[j] = v;
+    }
+    unsigned long long vol = 0, nb = 0;
+    for (uint32_t g = 0; g < s.nsegs; ++g) {
+        const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
+        const uint32_t* inv = s.segs[g].inv;
+        for (uint64_t i = a + t.rank(); i < b; i += t.size()) {
+            const uint32_t sid = inv[i];
+            if (!s.covered[sid]) {
+                s.covered[sid] = 1;
+                const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
+                s.newly[p] = sid;
+                vol += s.off[(uint64_t)sid + 1] - s.off[sid];
+            }
+        }
+    }
+    if (vol) {
+        atomicAdd(&s.vol_cov[j], vol);
+        atomicAdd(&s.vol_list[j], vol);
+    }
+    vol = 0;
+    const uint32_t wv = v >> 5, bit = 1u << (v & 31);
+    for (uint64_t b = t.rank(); b < s.nbmp; b += t.size()) {
+        const uint32_t sid = s.bmp_set[b];
+        if (!s.covered[sid] && (s.bmp[b * s.words + wv] & bit)) {
+            s.covered[sid] = 1;
+            const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
+            s.newly[p] = sid;
+            vol += s.bmp_len[b];
+            ++nb;
+        }
+    }
+    if (vol) atomicAdd(&s.vol_cov[j], vol);
+    if (nb) atomicAdd(&s.bmp_cov[j], nb);
+}
+
+template <class Team>
+__device__ void team_decrement(const SelectState& s, uint32_t j, Team t)
+{
+    const uint64_t cnt = s.newly_n[j];
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = t.rank() >> 5, nw = t.size() >> 5;
+    for (uint64_t first = gw * 32; first < cnt; first += nw * 32) {
+        const uint64_t i = first + lane;
+        uint64_t start = 0;
+        uint32_t len = 0, bid = kEmpty;
+        if (i < cnt) {
+            const uint32_t sid = s.newly[i];
+            start = s.off[sid];
+            len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+            bid = s.set_bmp[sid];
+        }
+        warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);
+        uint32_t bm = __ballot_sync(kFull, bid != kEmpty);
+        while (bm) {
+            const int o = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const uint32_t B = __shfl_sync(kFull, bid, o);
+            const uint32_t* row = s.bmp + (uint64_t)B * s.words;
+            for (uint32_t w = lane; w < s.words; w += 32) {
+                uint32_t x = row[w];
+                while (x) {
+                    const int tt = __ffs(x) - 1;
+                    x &= x - 1;
+                    atomicAdd(&s.work[w * 32 + tt], 0xFFFFFFFFu);
+                }
+            }
+        }
+    }
+}
+
+template <class Team>
+__device__ void team_rebuild_add(const SelectState& s, Team t)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = t.rank() >> 5, nw = t.size() >> 5;
+    for (uint64_t first = gw * 32; first < s.nsets; first += nw * 32) {
+        const uint64_t sid = first + lane;
+        uint64_t start = 0;
+        uint32_t len = 0;
+        if (sid < s.nsets && !s.covered[sid]) {
+            start = s.off[sid];
+            len = (uint32_t)(s.off[sid + 1] - start);
+        }
+        warp_apply_sets(s.arena, start, len, s.work, 1u);
+    }
+    // uncovered bitmap sets, by columns: items = (word, chunk of bitmaps)
+    if (s.nbmp == 0) return;
+    uint64_t chunks = t.size() / s.words;
+    if (chunks == 0) chunks = 1;
+    if (chunks > s.nbmp) chunks = s.nbmp;
+    const uint64_t per = (s.nbmp + chunks - 1) / chunks;
+    const uint64_t items = (uint64_t)s.words * chunks;
+    for (uint64_t it = t.rank(); it < items; it += t.size()) {
+        const uint32_t w = (uint32_t)(it % s.words);
+        const uint64_t b0 = (it / s.words) * per;
+        const uint64_t b1 = b0 + per < s.nbmp ? b0 + per : s.nbmp;
+        uint32_t c[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) c[i] = 0;
+        for (uint64_t b = b0; b < b1; ++b) {
+            if (s.covered[s.bmp_set[b]]) continue;
+            const uint32_t x = s.bmp[b * s.words + w];
+            if (!x) continue;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) c[i] += (x >> i) & 1u;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t v = w * 32 + i;
+            if (c[i] && v < s.n) atomicAdd(&s.work[v], c[i]);
+        }
+    }
+}
+
+template <class Team>
+__device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_mode)
+{
+    for (uint32_t j = 0; j < k; ++j) {
+        team_argmax(s, j, t);
+        t.sync();
+        team_cover(s, j, t);
+        t.sync();
+        if (threadIdx.x == 0) *s_mode = round_mode(s, j);
+        __syncthreads();
+        if (*s_mode == kModeDecrement) {
+            team_decrement(s, j, t);
+        } else {
+            for (uint64_t v = t.rank(); v < s.n; v += t.size()) s.work[v] = 0;
+            t.sync();
+            team_rebuild_add(s, t);
+        }
+        t.sync();
+    }
+}
+
+__global__ void __launch_bounds__(512)
+select_coop_kernel(SelectState s, uint32_t k)
+{
+    __shared__ int s_mode;
+    select_rounds(s, k, GridTeam{}, &s_mode);
+}
+
+__global__ void __launch_bounds__(512, 1)
+select_cta_kernel(const SelectState* states, const uint32_t* ks, uint32_t count)
+{
+    __shared__ int s_mode;
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        select_rounds(states[i], ks[i], BlockTeam{}, &s_mode);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_coop_kernel, 512, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    unsigned grid = (unsigned)(di.sms * per_sm);
+    SelectState sc = s;
+    uint32_t kk = k;
+    void* args[] = {&sc, &kk};
+    return cudaLaunchCooperativeKernel((void*)select_coop_kernel, dim3(grid), dim3(512), args, 0, st);
+}
+
+cudaError_t launch_select_batch(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,
+                                const DeviceInfo& di, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    select_cta_kernel<<<count, 512, 0, st>>>(d_states, d_ks, count);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
