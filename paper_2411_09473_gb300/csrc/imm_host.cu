@@ -86,7 +86,7 @@ struct imm_ctx {
     DBuf hist, cursor, vtmp;
 
     // selection scratch
-    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, vol_list, bmp_cov, seeds, dsegs;
+    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, vol_list, bmp_cov, ubmp, ubmp_n, seeds, dsegs;
 
     DBuf flags;
     uint64_t arena_limit = 0;
@@ -589,6 +589,8 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     TRY(ensure(c, c->vol_cov, (size_t)k * 8));
     TRY(ensure(c, c->vol_list, (size_t)k * 8));
     TRY(ensure(c, c->bmp_cov, (size_t)k * 8));
+    TRY(ensure(c, c->ubmp, std::max<uint64_t>(c->nbmp, 1) * 4));
+    TRY(ensure(c, c->ubmp_n, (size_t)k * 8));
     TRY(ensure(c, c->seeds, (size_t)k * 4));
     std::vector<DevSegment> hsegs;
     for (auto& s : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(s.voff), P<uint32_t>(s.inv)});
@@ -606,6 +608,7 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     CK(cudaMemsetAsync(c->vol_cov.p, 0, (size_t)k * 8, c->stream));
     CK(cudaMemsetAsync(c->vol_list.p, 0, (size_t)k * 8, c->stream));
     CK(cudaMemsetAsync(c->bmp_cov.p, 0, (size_t)k * 8, c->stream));
+    CK(cudaMemsetAsync(c->ubmp_n.p, 0, (size_t)k * 8, c->stream));
 
     SelectState s;
     s.n = c->n;
@@ -629,6 +632,8 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     s.vol_cov = P<unsigned long long>(c->vol_cov);
     s.vol_list = P<unsigned long long>(c->vol_list);
     s.bmp_cov = P<unsigned long long>(c->bmp_cov);
+    s.ubmp = P<uint32_t>(c->ubmp);
+    s.ubmp_n = P<unsigned long long>(c->ubmp_n);
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
@@ -709,7 +714,8 @@ void imm_destroy(imm_ctx* c)
     DBuf* bufs[] = {&c->off,      &c->arena,   &c->set_len,  &c->set_pos, &c->set_edges, &c->set_kind,
                     &c->large_q,  &c->bmp_rel, &c->stage,    &c->big,     &c->scalars,   &c->scan_tmp,
                     &c->covered,  &c->newly,   &c->keys,     &c->newly_n, &c->vol_cov,   &c->vol_list,
-                    &c->bmp_cov,  &c->seeds,   &c->dsegs,    &c->flags,   &c->set_bmp,   &c->bmp,
+                    &c->bmp_cov,  &c->ubmp,    &c->ubmp_n,   &c->seeds,   &c->dsegs,     &c->flags,
+                    &c->set_bmp,  &c->bmp,
                     &c->bmp_set,  &c->bmp_len};
     for (DBuf* b : bufs) dfree(c, *b);
     cudaStreamSynchronize(c->stream);

@@ -198,6 +198,8 @@ struct SelectState {
     unsigned long long* vol_cov;   // k: members of the sets covered per round
     unsigned long long* vol_list;  // k: of which in list-stored sets
     unsigned long long* bmp_cov;   // k: bitmap sets covered per round
+    uint32_t* ubmp;                // nbmp: uncovered bitmap ids gathered for a rebuild
+    unsigned long long* ubmp_n;    // k: entries of ubmp gathered in round j
     uint32_t* seeds;     // k
     const DevSegment* segs;
     uint32_t nsegs;

@@ -405,23 +405,40 @@ __device__ void team_rebuild_add(const SelectState& s, Team t)
         }
         warp_apply_sets(s.arena, start, len, s.work, 1u);
     }
-    // uncovered bitmap sets, by columns: items = (word, chunk of bitmaps)
-    if (s.nbmp == 0) return;
+}
+
+// Rebuild, bitmap part: gather the uncovered bitmaps of round j into ubmp,
+// then add them by columns (items = (word, chunk of gathered bitmaps)).
+template <class Team>
+__device__ void team_gather_uncovered(const SelectState& s, uint32_t j, Team t)
+{
+    for (uint64_t b = t.rank(); b < s.nbmp; b += t.size()) {
+        if (!s.covered[s.bmp_set[b]]) {
+            const unsigned long long p = atomicAdd(&s.ubmp_n[j], 1ull);
+            s.ubmp[p] = (uint32_t)b;
+        }
+    }
+}
+
+template <class Team>
+__device__ void team_count_uncovered(const SelectState& s, uint32_t j, Team t)
+{
+    const uint64_t nb = s.ubmp_n[j];
+    if (nb == 0) return;
     uint64_t chunks = t.size() / s.words;
     if (chunks == 0) chunks = 1;
-    if (chunks > s.nbmp) chunks = s.nbmp;
-    const uint64_t per = (s.nbmp + chunks - 1) / chunks;
+    if (chunks > nb) chunks = nb;
+    const uint64_t per = (nb + chunks - 1) / chunks;
     const uint64_t items = (uint64_t)s.words * chunks;
     for (uint64_t it = t.rank(); it < items; it += t.size()) {
         const uint32_t w = (uint32_t)(it % s.words);
         const uint64_t b0 = (it / s.words) * per;
-        const uint64_t b1 = b0 + per < s.nbmp ? b0 + per : s.nbmp;
+        const uint64_t b1 = b0 + per < nb ? b0 + per : nb;
         uint32_t c[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) c[i] = 0;
-        for (uint64_t b = b0; b < b1; ++b) {
-            if (s.covered[s.bmp_set[b]]) continue;
-            const uint32_t x = s.bmp[b * s.words + w];
+        for (uint64_t bi = b0; bi < b1; ++bi) {
+            const uint32_t x = s.bmp[(uint64_t)s.ubmp[bi] * s.words + w];
             if (!x) continue;
 #pragma unroll
             for (int i = 0; i < 32; ++i) c[i] += (x >> i) & 1u;
@@ -448,8 +465,10 @@ __device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_m
             team_decrement(s, j, t);
         } else {
             for (uint64_t v = t.rank(); v < s.n; v += t.size()) s.work[v] = 0;
+            if (s.nbmp) team_gather_uncovered(s, j, t);
             t.sync();
             team_rebuild_add(s, t);
+            if (s.nbmp) team_count_uncovered(s, j, t);
         }
         t.sync();
     }
