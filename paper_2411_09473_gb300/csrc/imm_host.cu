@@ -50,7 +50,7 @@ struct imm_ctx {
     uint32_t n = 0;
     uint64_t m = 0;
     int model = IMM_IC;
-    DBuf row, src, thr;
+    DBuf row, src, thr, guide;
 
     // RRR-set stream
     bool have_stream = false;
@@ -239,6 +239,7 @@ void free_graph(imm_ctx* c)
     dfree(c, c->row);
     dfree(c, c->src);
     dfree(c, c->thr);
+    dfree(c, c->guide);
     dfree(c, c->cnt);
     dfree(c, c->cnt_list);
     dfree(c, c->hist);
@@ -260,6 +261,7 @@ DevGraph dev_graph(imm_ctx* c)
     g.row = P<uint64_t>(c->row);
     g.src = P<uint32_t>(c->src);
     g.thr = P<uint32_t>(c->thr);
+    g.guide = P<uint32_t>(c->guide);
     return g;
 }
 
@@ -315,6 +317,10 @@ int load_graph_common(imm_ctx* c, uint32_t n, uint64_t m, const void* row, const
     if (flags) {
         free_graph(c);
         return set_err(c, IMM_EINVAL, "LT in-weights of some head sum to more than 1 + 1e-6");
+    }
+    if (model == IMM_LT) {
+        TRY(dalloc(c, c->guide, m_pad * 4));
+        CK(launch_lt_guide(P<uint64_t>(c->row), P<uint32_t>(c->thr), n, P<uint32_t>(c->guide), c->stream));
     }
     c->n = n;
     c->m = m;

@@ -83,4 +83,31 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
     return cudaGetLastError();
 }
 
+// LT guide table (index-assisted inverse transform; Chen & Asau 1974): for a
+// head v of in-degree d, bucket b < d covers the 24-bit draws r with
+// floor(r * d / 2^24) = b, whose smallest is lo_b = ceil(b * 2^24 / d), and
+// guide[row[v] + b] = first j with cthr[j] > lo_b.  A draw r in bucket b then
+// finds the first j with r < cthr[j] by scanning forward from guide[.]:
+// the same answer as a search over all of v's in-edges, in ~1-2 reads.
+__global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, uint32_t n, uint32_t* guide)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t rs = (uint32_t)row[v], re = (uint32_t)row[v + 1];
+        const uint64_t d = re - rs;
+        uint32_t j = rs;
+        for (uint64_t b = 0; b < d; ++b) {
+            const uint64_t lo = ((b << 24) + d - 1) / d;
+            while (j < re && (uint64_t)cthr[j] <= lo) ++j;
+            guide[rs + b] = j;
+        }
+    }
+}
+
+cudaError_t launch_lt_guide(const uint64_t* row, const uint32_t* cthr, uint32_t n, uint32_t* guide, cudaStream_t st)
+{
+    lt_guide_kernel<<<(n + 255) / 256, 256, 0, st>>>(row, cthr, n, guide);
+    return cudaGetLastError();
+}
+
 }  // namespace imm

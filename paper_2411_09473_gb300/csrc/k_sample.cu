@@ -625,15 +625,15 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 // ===========================================================================
 constexpr int kLtThreads = 128;
 
-// first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi
-__device__ __forceinline__ uint32_t lt_pick(const uint32_t* cthr, uint32_t lo, uint32_t hi, uint32_t r)
+// first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi: the
+// guide table gives a start no later than the answer, then a short scan
+__device__ __forceinline__ uint32_t lt_pick(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r)
 {
-    while (lo < hi) {
-        const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (r < __ldg(cthr + mid)) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
+    if (hi == lo) return hi;
+    const uint32_t d = hi - lo;
+    uint32_t j = __ldg(g.guide + lo + (uint32_t)(((uint64_t)r * d) >> 24));
+    while (j < hi && r >= __ldg(g.thr + j)) ++j;
+    return j;
 }
 
 __global__ void __launch_bounds__(kLtThreads)
@@ -674,7 +674,7 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), v, kTagLT), key);
         uint32_t lo, hi;
         edge_range(g, v, lo, hi);
-        const uint32_t pick = lt_pick(g.thr, lo, hi, w.x >> 8);
+        const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8);
         bool stop = pick == hi;
         uint32_t u = 0;
         if (!stop) {
@@ -748,7 +748,7 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                 const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), v, kTagLT), key);
                 uint32_t lo, hi;
                 edge_range(g, v, lo, hi);
-                const uint32_t pick = lt_pick(g.thr, lo, hi, w.x >> 8);
+                const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8);
                 if (pick == hi) break;
                 const uint32_t u = __ldg(g.src + pick);
                 const uint32_t bit = 1u << (u & 31);

@@ -297,8 +297,26 @@ struct BlockTeam {
 template <class Team>
 __device__ void team_argmax(const SelectState& s, uint32_t j, Team t)
 {
+    // four vertices per step with 16-byte count loads (work is 256-byte
+    // aligned); the ragged tail one by one
     unsigned long long best = 0;
-    for (uint64_t v = t.rank(); v < s.n; v += t.size()) {
+    const uint64_t n4 = s.n >> 2;
+    const uint4* w4 = reinterpret_cast<const uint4*>(s.work);
+    const uint32_t* p4 = reinterpret_cast<const uint32_t*>(s.picked);
+    for (uint64_t i = t.rank(); i < n4; i += t.size()) {
+        const uint4 w = w4[i];
+        const uint32_t pk = p4[i];
+        const uint32_t v = (uint32_t)(i << 2);
+        const uint32_t c[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!((pk >> (8 * q)) & 0xFFu)) {
+                const unsigned long long key = ((unsigned long long)c[q] << 32) | (0xFFFFFFFFu - (v + q));
+                best = key > best ? key : best;
+            }
+        }
+    }
+    for (uint64_t v = (n4 << 2) + t.rank(); v < s.n; v += t.size()) {
         if (!s.picked[v]) {
             const unsigned long long key = ((unsigned long long)s.work[v] << 32) | (0xFFFFFFFFu - (uint32_t)v);
             best = key > best ? key : best;

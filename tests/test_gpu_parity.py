@@ -290,3 +290,23 @@ def test_arena_limit_enomem_then_recovers(imm):
     imm.imm_set_arena_limit(ctx, 0)
     imm.imm_reset_sets(ctx)
     check_stream(imm, ctx, g, 2000, 5)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_lt_uneven_weights_and_none_mass(imm, seed):
+    # per-head weights drawn unevenly, summing to U(0.3, 1.0): exercises the
+    # walker's threshold search on ragged cumulative thresholds and on "none"
+    rng = np.random.default_rng(50 + seed)
+    g0 = graphgen.make_graph(3000, 40000, 60 + seed, LT, "inv_indeg")
+    w = np.zeros(g0.m, dtype=np.float32)
+    for v in range(g0.n):
+        lo, hi = int(g0.row[v]), int(g0.row[v + 1])
+        if hi > lo:
+            x = rng.exponential(1.0, hi - lo)
+            w[lo:hi] = (x / x.sum() * rng.uniform(0.3, 1.0)).astype(np.float32) * np.float32(0.999)
+    g = graphgen.Graph(n=g0.n, row=g0.row, src=g0.src, weight=w, model=LT)
+    ctx = new_ctx(imm, g)
+    o = check_stream(imm, ctx, g, 20000, seed)
+    seeds, cov = imm.imm_select(ctx, 30)
+    want, wcov = o.select(30)
+    assert np.array_equal(seeds, want) and cov == wcov
