@@ -34,6 +34,7 @@ struct Segment {
 };
 
 constexpr double kE = 2.71828182845904523536;  // the double nearest e
+constexpr uint32_t kSelectCtaMaxN = 1u << 17;  // graphs this small select in one CTA
 
 }  // namespace
 
@@ -86,7 +87,7 @@ struct imm_ctx {
     DBuf hist, cursor, vtmp;
 
     // selection scratch
-    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, vol_list, bmp_cov, ubmp, ubmp_n, seeds, dsegs;
+    DBuf work, picked, covered, newly, keys, newly_n, vol_cov, vol_list, bmp_cov, ubmp, ubmp_n, seeds, dsegs, dstate;
 
     DBuf flags;
     uint64_t arena_limit = 0;
@@ -643,8 +644,30 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
-    // all k rounds in one cooperative launch; per-round launches if the
-    // device refuses a cooperative grid of that size
+    // all k rounds in one launch: one CTA for small graphs (block barriers),
+    // the whole cooperative grid otherwise; per-round launches if the device
+    // refuses a cooperative grid of that size
+    if (c->n <= kSelectCtaMaxN) {
+        TRY(ensure(c, c->dstate, sizeof(SelectState) + 16));
+        CK(cudaMemcpyAsync(c->dstate.p, &s, sizeof(SelectState), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(c->dstate.p) + sizeof(SelectState), &k, 4,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(launch_select_batch(P<SelectState>(c->dstate),
+                               reinterpret_cast<const uint32_t*>(reinterpret_cast<char*>(c->dstate.p) +
+                                                                 sizeof(SelectState)),
+                               1, c->di, c->stream));
+        c->acc_launches += 1;
+        CK(cudaEventRecord(c->ev[1], c->stream));
+        std::vector<unsigned long long> nn0(k);
+        CK(cudaMemcpyAsync(seeds_out, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(nn0.data(), c->newly_n.p, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->acc_select_ms += elapsed(c, 0, 1);
+        uint64_t cov0 = 0;
+        for (uint32_t j = 0; j < k; ++j) cov0 += nn0[j];
+        if (covered_out) *covered_out = cov0;
+        return IMM_OK;
+    }
     const cudaError_t ce = launch_select_all(s, k, c->di, c->stream);
     if (ce == cudaErrorCooperativeLaunchTooLarge || ce == cudaErrorNotSupported) {
         cudaGetLastError();
@@ -721,7 +744,7 @@ void imm_destroy(imm_ctx* c)
                     &c->large_q,  &c->bmp_rel, &c->stage,    &c->big,     &c->scalars,   &c->scan_tmp,
                     &c->covered,  &c->newly,   &c->keys,     &c->newly_n, &c->vol_cov,   &c->vol_list,
                     &c->bmp_cov,  &c->ubmp,    &c->ubmp_n,   &c->seeds,   &c->dsegs,     &c->flags,
-                    &c->set_bmp,  &c->bmp,
+                    &c->set_bmp,  &c->bmp,     &c->dstate,
                     &c->bmp_set,  &c->bmp_len};
     for (DBuf* b : bufs) dfree(c, *b);
     cudaStreamSynchronize(c->stream);
