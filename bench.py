@@ -37,7 +37,7 @@ METRIC = "IMM seconds-to-seeds"
 # (profiles/ic_large_kernel__ic_u01_1m_first2000sets.md: 12.454 GB over
 # 4,620,412,076 in-edges).  Traffic of a full launch is scaled by its in-edges.
 IC_LARGE_DRAM_BYTES_PER_EDGE = 12.454e9 / 4620412076
-WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k")
+WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "batch64")
 
 
 def parse():
@@ -386,12 +386,88 @@ def run_gpu(args, dist: Dist):
     imm.imm_destroy(ctx)
 
 
+def run_batch(args, dist: Dist):
+    """64 independent IMM instances (R-MAT, n log-uniform over 2^10..2^18,
+    average degree 8..32, IC/LT alternating, k 5..100, eps 0.1..0.5), one
+    step = the whole batch through imm_run_batch; the one-at-a-time path
+    (imm_run per instance, in order) is timed beside it."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_2411_09473_gb300 import imm
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    b = graphgen.batch_workload(count=64)
+    ctxs = []
+    for g in b.graphs:
+        c = imm.imm_create(device=dev, stream=stream)
+        imm.imm_load_graph(c, g.n, g.m, g.row, g.src, g.weight, g.model)
+        ctxs.append(c)
+    queries = [(ctxs[q.graph_id], q.k, q.epsilon, q.ell, q.seed) for q in b.queries]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        seeds, stats, status = imm.imm_run_batch(queries)
+        assert status == [0] * len(queries), status
+    clocks = ClockSampler(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seeds, stats, status = imm.imm_run_batch(queries)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    dist.barrier()
+    clk = clocks.stop()
+    step_s = dist.max(statistics.mean(times))
+    # one at a time, same instances, same results
+    solo = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, q in enumerate(b.queries):
+            g = b.graphs[q.graph_id]
+            s2, _ = imm.imm_run(ctxs[q.graph_id], g.model, q.k, q.epsilon, q.ell, q.seed)
+            if rep == 0:
+                assert np.array_equal(s2, seeds[i]), i
+        torch.cuda.synchronize()
+        solo.append(time.perf_counter() - t0)
+    solo_s = min(solo)
+    if dist.rank == 0:
+        nq = len(queries)
+        line = {
+            "metric": "batched IMM queries/s", "value": dist.sum(nq / step_s) if dist.world > 1 else nq / step_s,
+            "unit": "queries/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "64 IMM instances: R-MAT n=2^U(10,18), avg degree U(8,32), IC/LT alternating, "
+                                   "k=U{5..100}, eps=U(0.1,0.5), batch seed 4", "l2": "256 MB write between steps",
+                       "parallelism": f"replicas x{dist.world}"},
+            "one_at_a_time": {"value": nq / solo_s, "unit": "queries/s", "s_per_batch": solo_s,
+                              "results_identical": True},
+            "batched_over_solo": solo_s / step_s,
+            "theta_total": int(sum(st.num_sets for st in stats)),
+            "members_total": int(sum(st.members for st in stats)),
+            "roofline": None, "roofline_note": "many small overlapping instances; see the plain workloads",
+            "gpu_launches": None, "clocks": clk, "e2e": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.workload == "batch64":
+            run_batch(args, dist)
         else:
             run_gpu(args, dist)
     finally:

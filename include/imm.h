@@ -160,6 +160,32 @@ int imm_select(imm_ctx* ctx, uint32_t k, uint32_t* seeds_out, uint64_t* covered_
 int imm_run(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell,
             uint64_t rng_seed, uint32_t* seeds_out, imm_stats* stats_out);
 
+/* One query of a batch: the context holding its graph (loaded with
+ * imm_load_graph; the model is the graph's), and IMM's parameters. */
+typedef struct imm_query {
+    imm_ctx* graph;
+    uint32_t k;
+    double epsilon;
+    double ell;
+    uint64_t rng_seed;
+} imm_query;
+
+/* Batched IMM (Alg. 1 per query, as imm_run): nq queries over one or more
+ * loaded graphs advance together.  Each wave runs one sampling batch of every
+ * query still sampling (each on its own stream) and one selection launch for
+ * every query that reached its sampling target (one CTA per query).  Each
+ * query's seeds, theta ladder, LB and theta equal imm_run's on the same
+ * inputs.  seeds_out (host) receives the queries' seeds concatenated in query
+ * order (sum of k entries); stats_out (host, nq entries, nullable) and
+ * status_out (host, nq entries, nullable) receive per-query statistics and
+ * status.  The graph contexts' RRR-set streams are not touched.
+ * Errors: EINVAL (a query's graph missing or not loaded, contexts on
+ * different devices, bad k/epsilon/ell); a query that fails on its own
+ * (ENOMEM under the graph context's arena limit, ...) reports its status in
+ * status_out while the others complete. */
+int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* seeds_out, imm_stats* stats_out,
+                  int* status_out);
+
 /* Drop the RRR-set stream (counts, arena, index); keeps the graph. */
 int imm_reset_sets(imm_ctx* ctx);
 

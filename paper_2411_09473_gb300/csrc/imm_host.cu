@@ -46,8 +46,11 @@ struct imm_ctx {
     DeviceInfo di{};
     std::string err = "no error";
 
-    // graph
+    // graph (a worker context of a batch borrows its parent's graph arrays)
     bool loaded = false;
+    bool borrowed = false;
+    bool own_stream = false;
+    DBuf bstates;  // batch engine: device copies of the selection states
     uint32_t n = 0;
     uint64_t m = 0;
     int model = IMM_IC;
@@ -97,7 +100,23 @@ struct imm_ctx {
     // accounting for imm_stats
     double acc_sample_ms = 0, acc_select_ms = 0, acc_index_ms = 0;
     uint64_t acc_sample_launches = 0, acc_launches = 0, acc_edges = 0, acc_sample_members = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[8] = {};
+    bool index_timed = false;
+
+    // batch in flight (phases 1-3) and pinned host slots for its read-backs
+    SampleBatch fb{};
+    BatchOut fo{};
+    uint32_t fb_large = 0;
+    struct Pinned {
+        uint32_t large_count;
+        uint32_t k;
+        BatchScalars sc;
+        SelectState state;
+    };
+    Pinned* pin = nullptr;
+    uint32_t* pin_seeds = nullptr;
+    unsigned long long* pin_newly = nullptr;
+    uint32_t pin_k = 0;
 };
 
 namespace {
@@ -207,10 +226,12 @@ T* P(const DBuf& b)
     return reinterpret_cast<T*>(b.p);
 }
 
+// device time between two recorded events; 0 unless both have completed
 double elapsed(imm_ctx* c, int a, int b)
 {
+    if (cudaEventQuery(c->ev[b]) != cudaSuccess || cudaEventQuery(c->ev[a]) != cudaSuccess) return 0.0;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]);
+    if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) return 0.0;
     return (double)ms;
 }
 
@@ -237,6 +258,10 @@ void drop_stream(imm_ctx* c)
 void free_graph(imm_ctx* c)
 {
     drop_stream(c);
+    if (c->borrowed) {
+        c->row = c->src = c->thr = c->guide = DBuf{};
+        c->borrowed = false;
+    }
     dfree(c, c->row);
     dfree(c, c->src);
     dfree(c, c->thr);
@@ -386,8 +411,16 @@ int merge_segments(imm_ctx* c)
     return IMM_OK;
 }
 
-// Generate_RRRsets: extend the stream to theta sets.
-int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
+// ---------------------------------------------------------------------------
+// Generate_RRRsets, one batch of consecutive set ids in three phases so that
+// many contexts (each on its own stream) can advance together:
+//   phase 1  buffers, small-set path launch, large-set count -> pinned host
+//   phase 2  (after the stream drained) large-set path and batch scan,
+//            batch scalars -> pinned host
+//   phase 3  (after the stream drained) grow the arena / bitmap arena, launch
+//            compaction, bitmap store, vertex scan and index scatter
+// ---------------------------------------------------------------------------
+int begin_stream(imm_ctx* c, uint64_t theta, uint64_t seed)
 {
     if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
     if (theta >= 0xFFFFFFFFull) return set_err(c, IMM_EINVAL, "theta must be < 2^32-1");
@@ -395,197 +428,245 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
         return set_err(c, IMM_ESTATE, "rng seed differs from the current stream's; reset first");
     c->have_stream = true;
     c->seed = seed;
-    const DevGraph g = dev_graph(c);
-    const bool ic = c->model == IMM_IC;
-    const uint32_t words = (uint32_t)(((uint64_t)c->n + 31) / 32);
     TRY(ensure(c, c->scalars, sizeof(BatchScalars)));
     TRY(ensure(c, c->hist, (size_t)c->n * 4));
     TRY(ensure(c, c->cursor, (size_t)c->n * 4));
     TRY(ensure(c, c->vtmp, scan_tmp_words(c->n) * 8));
-
-    while (c->nsets < theta) {
-        const uint64_t want = theta - c->nsets;
-        uint32_t count = (uint32_t)std::min<uint64_t>(want, c->next_batch);
-        if (count == 0) count = 1;
-        // batch buffers
-        if (c->batch_cap < count) {
-            const uint32_t cap = std::max(count, c->batch_cap + c->batch_cap / 2);
-            TRY(dalloc(c, c->set_len, (size_t)cap * 4));
-            TRY(dalloc(c, c->set_pos, (size_t)cap * 8));
-            TRY(dalloc(c, c->set_edges, (size_t)cap * 4));
-            TRY(dalloc(c, c->set_kind, (size_t)cap * 4));
-            TRY(dalloc(c, c->large_q, (size_t)cap * 4));
-            TRY(dalloc(c, c->bmp_rel, (size_t)cap * 4));
-            TRY(dalloc(c, c->scan_tmp, scan_tmp_words(cap) * 8));
-            c->batch_cap = cap;
-        }
-        // small-path staging: every small set holds at most small_cap members
-        const uint64_t stage_need = (uint64_t)count * small_cap(c->model);
-        if (c->stage_cap < stage_need) {
-            TRY(ensure(c, c->stage, stage_need * 4));
-            c->stage_cap = c->stage.bytes / 4;
-        }
-        // per-set arrays of the stream: room for base + count sets
-        if (c->off_cap < c->nsets + count) {
-            const uint64_t need = c->nsets + count;
-            const uint64_t cap = std::max(need, c->off_cap + c->off_cap / 2);
-            TRY(grow_keep(c, c->off, (cap + 1) * 8, (c->nsets + 1) * 8));
-            TRY(grow_keep(c, c->set_bmp, cap * 4, c->nsets * 4));
-            c->off_cap = cap;
-        }
-
-        BatchScalars* sc = P<BatchScalars>(c->scalars);
-        CK(cudaMemsetAsync(sc, 0, sizeof(BatchScalars), c->stream));
-        CK(cudaMemsetAsync(&sc->first_fail, 0xFF, 4, c->stream));
-        SampleBatch b;
-        b.seed = seed;
-        b.base = c->nsets;
-        b.count = count;
-        b.words = words;
-        b.set_len = P<uint32_t>(c->set_len);
-        b.set_pos = P<uint64_t>(c->set_pos);
-        b.set_edges = P<uint32_t>(c->set_edges);
-        b.set_kind = P<uint32_t>(c->set_kind);
-        b.stage = P<uint32_t>(c->stage);
-        b.stage_cap = c->stage_cap;
-        b.big = P<uint32_t>(c->big);
-        b.big_cap = 0;
-        b.large_q = P<uint32_t>(c->large_q);
-        b.sc = sc;
-
-        CK(cudaEventRecord(c->ev[0], c->stream));
-        if (ic) CK(launch_ic_small(g, b, c->di, c->stream));
-        else CK(launch_lt_small(g, b, c->di, c->stream));
-        CK(cudaEventRecord(c->ev[1], c->stream));
-        uint32_t large_count = 0;
-        CK(cudaMemcpyAsync(&large_count, &sc->large_count, 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        c->acc_sample_ms += elapsed(c, 0, 1);
-        c->acc_sample_launches += 1;
-        c->acc_launches += 1;
-        if (large_count) {
-            // outputs of the large path: a list or a bitmap of `words` words
-            // each; capped by a memory budget (sets past the cap are resampled)
-            const uint64_t fr = device_free_bytes() + c->big.bytes;
-            const uint64_t budget = std::max<uint64_t>((uint64_t)words * 4,
-                                                       std::min<uint64_t>(fr / 4, 16ull << 30) / 4);
-            const uint64_t need = std::min<uint64_t>((uint64_t)large_count * words, budget);
-            if (c->big_cap < need) {
-                TRY(ensure(c, c->big, need * 4));
-                c->big_cap = c->big.bytes / 4;
-            }
-            b.big = P<uint32_t>(c->big);
-            b.big_cap = c->big_cap;
-            LargeSlots ls;
-            if (ic) {
-                const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
-                TRY(ensure_slots(c, (uint32_t)c->di.sms, !smem));
-            } else {
-                TRY(ensure_slots(c, (uint32_t)std::min(c->di.sms * 2, 1024), true));
-            }
-            ls.queues = P<uint32_t>(c->slot_q);
-            ls.queue_cap = c->n;
-            ls.bitmaps = P<uint32_t>(c->slot_bm);
-            ls.bitmap_words = words;
-            ls.nslots = std::min<uint32_t>(c->nslots, large_count);
-            CK(cudaEventRecord(c->ev[0], c->stream));
-            if (ic) CK(launch_ic_large(g, b, ls, c->di, c->stream));
-            else CK(launch_lt_long(g, b, ls, c->di, c->stream));
-            CK(cudaEventRecord(c->ev[1], c->stream));
-            c->acc_sample_launches += 1;
-            c->acc_launches += 1;
-        }
-        BatchOut o;
-        o.off = P<uint64_t>(c->off);
-        o.arena = P<uint32_t>(c->arena);
-        o.set_bmp = P<uint32_t>(c->set_bmp);
-        o.bmp = P<uint32_t>(c->bmp);
-        o.bmp_set = P<uint32_t>(c->bmp_set);
-        o.bmp_len = P<uint32_t>(c->bmp_len);
-        o.bmp_rel = P<uint32_t>(c->bmp_rel);
-        o.bmp_base = c->nbmp;
-        CK(cudaEventRecord(c->ev[2], c->stream));
-        CK(launch_batch_scan(b, o, P<uint64_t>(c->scan_tmp), c->di, c->stream));
-        c->acc_launches += 3;
-        BatchScalars hs;
-        CK(cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        if (large_count) c->acc_sample_ms += elapsed(c, 0, 1);
-        if (hs.error) return set_err(c, IMM_ECUDA, "sampler reported device error 0x%x", hs.error);
-        const uint64_t committed = hs.committed;
-        const uint64_t lm = hs.list_members;
-        const uint64_t nb = hs.nbitmaps;
-        if (committed == 0) {
-            if (count == 1) return set_err(c, IMM_ENOMEM, "output buffer cannot hold one RRR set");
-            c->next_batch = std::max<uint32_t>(1, count / 4);
-            continue;
-        }
-        // arena for the lists, bitmap arena, this batch's index segment
-        const uint64_t seg_bytes = ((uint64_t)c->n + 1) * 8 + lm * 4;
-        const uint64_t bmp_bytes = nb * words * 4;
-        if (c->arena_cap < c->list_members + lm) {
-            const uint64_t need = c->list_members + lm;
-            uint64_t cap = std::max(need, c->arena_cap + c->arena_cap / 2);
-            if (c->arena_limit && (cap * 4 + c->index_bytes + c->bmp.bytes + seg_bytes + bmp_bytes > c->arena_limit))
-                cap = need;
-            TRY(index_limit_ok(c, (cap - c->arena_cap) * 4 + seg_bytes + bmp_bytes));
-            TRY(grow_keep(c, c->arena, cap * 4, c->list_members * 4));
-            c->arena_cap = cap;
-        } else {
-            TRY(index_limit_ok(c, seg_bytes + bmp_bytes));
-        }
-        if (c->bmp_cap < c->nbmp + nb) {
-            const uint64_t need = c->nbmp + nb;
-            const uint64_t cap = std::max(need, c->bmp_cap + c->bmp_cap / 2);
-            TRY(grow_keep(c, c->bmp, cap * words * 4, c->nbmp * words * 4));
-            TRY(grow_keep(c, c->bmp_set, cap * 4, c->nbmp * 4));
-            TRY(grow_keep(c, c->bmp_len, cap * 4, c->nbmp * 4));
-            c->bmp_cap = cap;
-        }
-        o.arena = P<uint32_t>(c->arena);
-        o.bmp = P<uint32_t>(c->bmp);
-        o.bmp_set = P<uint32_t>(c->bmp_set);
-        o.bmp_len = P<uint32_t>(c->bmp_len);
-        Segment seg;
-        seg.set_begin = c->nsets;
-        seg.set_end = c->nsets + committed;
-        TRY(dalloc(c, seg.voff, ((size_t)c->n + 1) * 8));
-        if (dalloc(c, seg.inv, std::max<uint64_t>(lm, 1) * 4) != IMM_OK) {
-            dfree(c, seg.voff);
-            return IMM_ENOMEM;
-        }
-        CK(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n * 4, c->stream));
-        CK(launch_compact(b, o, committed, P<uint32_t>(c->hist), c->di, c->stream));
-        CK(launch_bitmap_store(b, o, nb, c->n, P<uint32_t>(c->cnt), c->di, c->stream));
-        CK(launch_vertex_scan(P<uint32_t>(c->hist), c->n, P<uint64_t>(seg.voff), P<uint32_t>(c->cnt),
-                              P<uint32_t>(c->cnt_list), P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di,
-                              c->stream));
-        CK(launch_index_scatter(seg.set_begin, seg.set_end, P<uint64_t>(c->off), P<uint32_t>(c->arena),
-                                P<uint64_t>(seg.voff), P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di,
-                                c->stream));
-        CK(cudaEventRecord(c->ev[3], c->stream));
-        c->acc_launches += nb ? 7 : 5;
-        c->index_bytes += seg.voff.bytes + seg.inv.bytes;
-        c->segs.push_back(seg);
-        c->nsets += committed;
-        c->list_members += lm;
-        c->nmembers += hs.all_members;
-        c->nbmp += nb;
-        c->acc_edges += hs.edges;
-        c->acc_sample_members += hs.all_members;
-        CK(cudaEventSynchronize(c->ev[3]));
-        c->acc_index_ms += elapsed(c, 2, 3);
-        c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : (1u << 22);
-        if (c->segs.size() > 48) TRY(merge_segments(c));
-    }
     return IMM_OK;
 }
 
-int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
+void take_index_time(imm_ctx* c)
+{
+    // the stream has drained since the index launches were recorded
+    if (c->index_timed && cudaEventQuery(c->ev[7]) == cudaSuccess) {
+        c->acc_index_ms += elapsed(c, 6, 7);
+        c->index_timed = false;
+    }
+}
+
+int batch_phase1(imm_ctx* c, uint64_t theta)
+{
+    take_index_time(c);
+    const uint32_t words = (uint32_t)(((uint64_t)c->n + 31) / 32);
+    const uint64_t want = theta - c->nsets;
+    uint32_t count = (uint32_t)std::min<uint64_t>(want, c->next_batch);
+    if (count == 0) count = 1;
+    if (c->batch_cap < count) {
+        const uint32_t cap = std::max(count, c->batch_cap + c->batch_cap / 2);
+        TRY(dalloc(c, c->set_len, (size_t)cap * 4));
+        TRY(dalloc(c, c->set_pos, (size_t)cap * 8));
+        TRY(dalloc(c, c->set_edges, (size_t)cap * 4));
+        TRY(dalloc(c, c->set_kind, (size_t)cap * 4));
+        TRY(dalloc(c, c->large_q, (size_t)cap * 4));
+        TRY(dalloc(c, c->bmp_rel, (size_t)cap * 4));
+        TRY(dalloc(c, c->scan_tmp, scan_tmp_words(cap) * 8));
+        c->batch_cap = cap;
+    }
+    // small-path staging: every small set holds at most small_cap members
+    const uint64_t stage_need = (uint64_t)count * small_cap(c->model);
+    if (c->stage_cap < stage_need) {
+        TRY(ensure(c, c->stage, stage_need * 4));
+        c->stage_cap = c->stage.bytes / 4;
+    }
+    // per-set arrays of the stream: room for base + count sets
+    if (c->off_cap < c->nsets + count) {
+        const uint64_t need = c->nsets + count;
+        const uint64_t cap = std::max(need, c->off_cap + c->off_cap / 2);
+        TRY(grow_keep(c, c->off, (cap + 1) * 8, (c->nsets + 1) * 8));
+        TRY(grow_keep(c, c->set_bmp, cap * 4, c->nsets * 4));
+        c->off_cap = cap;
+    }
+    BatchScalars* sc = P<BatchScalars>(c->scalars);
+    CK(cudaMemsetAsync(sc, 0, sizeof(BatchScalars), c->stream));
+    CK(cudaMemsetAsync(&sc->first_fail, 0xFF, 4, c->stream));
+    SampleBatch& b = c->fb;
+    b.seed = c->seed;
+    b.base = c->nsets;
+    b.count = count;
+    b.words = words;
+    b.set_len = P<uint32_t>(c->set_len);
+    b.set_pos = P<uint64_t>(c->set_pos);
+    b.set_edges = P<uint32_t>(c->set_edges);
+    b.set_kind = P<uint32_t>(c->set_kind);
+    b.stage = P<uint32_t>(c->stage);
+    b.stage_cap = c->stage_cap;
+    b.big = P<uint32_t>(c->big);
+    b.big_cap = 0;
+    b.large_q = P<uint32_t>(c->large_q);
+    b.sc = sc;
+    const DevGraph g = dev_graph(c);
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    if (c->model == IMM_IC) CK(launch_ic_small(g, b, c->di, c->stream));
+    else CK(launch_lt_small(g, b, c->di, c->stream));
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    CK(cudaMemcpyAsync(&c->pin->large_count, &sc->large_count, 4, cudaMemcpyDeviceToHost, c->stream));
+    c->acc_sample_launches += 1;
+    c->acc_launches += 1;
+    return IMM_OK;
+}
+
+int batch_phase2(imm_ctx* c)
+{
+    c->acc_sample_ms += elapsed(c, 0, 1);
+    SampleBatch& b = c->fb;
+    const uint32_t large_count = c->pin->large_count;
+    const uint32_t words = b.words;
+    c->fb_large = large_count;
+    if (large_count) {
+        // outputs of the large path: a list or a bitmap of `words` words
+        // each; capped by a memory budget (sets past the cap are resampled)
+        const uint64_t fr = device_free_bytes() + c->big.bytes;
+        const uint64_t budget = std::max<uint64_t>((uint64_t)words * 4,
+                                                   std::min<uint64_t>(fr / 4, 16ull << 30) / 4);
+        const uint64_t need = std::min<uint64_t>((uint64_t)large_count * words, budget);
+        if (c->big_cap < need) {
+            TRY(ensure(c, c->big, need * 4));
+            c->big_cap = c->big.bytes / 4;
+        }
+        b.big = P<uint32_t>(c->big);
+        b.big_cap = c->big_cap;
+        const bool ic = c->model == IMM_IC;
+        const uint32_t want_slots =
+            std::min<uint32_t>(large_count, ic ? (uint32_t)c->di.sms : (uint32_t)std::min(c->di.sms * 2, 1024));
+        if (ic) {
+            const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
+            TRY(ensure_slots(c, want_slots, !smem));
+        } else {
+            TRY(ensure_slots(c, want_slots, true));
+        }
+        LargeSlots ls;
+        ls.queues = P<uint32_t>(c->slot_q);
+        ls.queue_cap = c->n;
+        ls.bitmaps = P<uint32_t>(c->slot_bm);
+        ls.bitmap_words = words;
+        ls.nslots = std::min<uint32_t>(c->nslots, large_count);
+        const DevGraph g = dev_graph(c);
+        CK(cudaEventRecord(c->ev[2], c->stream));
+        if (ic) CK(launch_ic_large(g, b, ls, c->di, c->stream));
+        else CK(launch_lt_long(g, b, ls, c->di, c->stream));
+        CK(cudaEventRecord(c->ev[3], c->stream));
+        c->acc_sample_launches += 1;
+        c->acc_launches += 1;
+    }
+    BatchOut& o = c->fo;
+    o.off = P<uint64_t>(c->off);
+    o.arena = P<uint32_t>(c->arena);
+    o.set_bmp = P<uint32_t>(c->set_bmp);
+    o.bmp = P<uint32_t>(c->bmp);
+    o.bmp_set = P<uint32_t>(c->bmp_set);
+    o.bmp_len = P<uint32_t>(c->bmp_len);
+    o.bmp_rel = P<uint32_t>(c->bmp_rel);
+    o.bmp_base = c->nbmp;
+    CK(launch_batch_scan(b, o, P<uint64_t>(c->scan_tmp), c->di, c->stream));
+    c->acc_launches += 3;
+    CK(cudaMemcpyAsync(&c->pin->sc, b.sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, c->stream));
+    return IMM_OK;
+}
+
+// returns IMM_OK; *progress = false when the batch kept no set (retry smaller)
+int batch_phase3(imm_ctx* c, bool* progress)
+{
+    if (c->fb_large) c->acc_sample_ms += elapsed(c, 2, 3);
+    SampleBatch& b = c->fb;
+    BatchOut& o = c->fo;
+    const BatchScalars& hs = c->pin->sc;
+    const uint32_t words = b.words;
+    const uint32_t count = b.count;
+    *progress = false;
+    if (hs.error) return set_err(c, IMM_ECUDA, "sampler reported device error 0x%x", hs.error);
+    const uint64_t committed = hs.committed;
+    const uint64_t lm = hs.list_members;
+    const uint64_t nb = hs.nbitmaps;
+    if (committed == 0) {
+        if (count == 1) return set_err(c, IMM_ENOMEM, "output buffer cannot hold one RRR set");
+        c->next_batch = std::max<uint32_t>(1, count / 4);
+        return IMM_OK;
+    }
+    // arena for the lists, bitmap arena, this batch's index segment
+    const uint64_t seg_bytes = ((uint64_t)c->n + 1) * 8 + lm * 4;
+    const uint64_t bmp_bytes = nb * words * 4;
+    if (c->arena_cap < c->list_members + lm) {
+        const uint64_t need = c->list_members + lm;
+        uint64_t cap = std::max(need, c->arena_cap + c->arena_cap / 2);
+        if (c->arena_limit && (cap * 4 + c->index_bytes + c->bmp.bytes + seg_bytes + bmp_bytes > c->arena_limit))
+            cap = need;
+        TRY(index_limit_ok(c, (cap - c->arena_cap) * 4 + seg_bytes + bmp_bytes));
+        TRY(grow_keep(c, c->arena, cap * 4, c->list_members * 4));
+        c->arena_cap = cap;
+    } else {
+        TRY(index_limit_ok(c, seg_bytes + bmp_bytes));
+    }
+    if (c->bmp_cap < c->nbmp + nb) {
+        const uint64_t need = c->nbmp + nb;
+        const uint64_t cap = std::max(need, c->bmp_cap + c->bmp_cap / 2);
+        TRY(grow_keep(c, c->bmp, cap * words * 4, c->nbmp * words * 4));
+        TRY(grow_keep(c, c->bmp_set, cap * 4, c->nbmp * 4));
+        TRY(grow_keep(c, c->bmp_len, cap * 4, c->nbmp * 4));
+        c->bmp_cap = cap;
+    }
+    o.arena = P<uint32_t>(c->arena);
+    o.bmp = P<uint32_t>(c->bmp);
+    o.bmp_set = P<uint32_t>(c->bmp_set);
+    o.bmp_len = P<uint32_t>(c->bmp_len);
+    Segment seg;
+    seg.set_begin = c->nsets;
+    seg.set_end = c->nsets + committed;
+    TRY(dalloc(c, seg.voff, ((size_t)c->n + 1) * 8));
+    if (dalloc(c, seg.inv, std::max<uint64_t>(lm, 1) * 4) != IMM_OK) {
+        dfree(c, seg.voff);
+        return IMM_ENOMEM;
+    }
+    CK(cudaEventRecord(c->ev[6], c->stream));
+    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n * 4, c->stream));
+    CK(launch_compact(b, o, committed, P<uint32_t>(c->hist), c->di, c->stream));
+    CK(launch_bitmap_store(b, o, nb, c->n, P<uint32_t>(c->cnt), c->di, c->stream));
+    CK(launch_vertex_scan(P<uint32_t>(c->hist), c->n, P<uint64_t>(seg.voff), P<uint32_t>(c->cnt),
+                          P<uint32_t>(c->cnt_list), P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di,
+                          c->stream));
+    CK(launch_index_scatter(seg.set_begin, seg.set_end, P<uint64_t>(c->off), P<uint32_t>(c->arena),
+                            P<uint64_t>(seg.voff), P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di, c->stream));
+    CK(cudaEventRecord(c->ev[7], c->stream));
+    c->index_timed = true;
+    c->acc_launches += nb ? 7 : 5;
+    c->index_bytes += seg.voff.bytes + seg.inv.bytes;
+    c->segs.push_back(seg);
+    c->nsets += committed;
+    c->list_members += lm;
+    c->nmembers += hs.all_members;
+    c->nbmp += nb;
+    c->acc_edges += hs.edges;
+    c->acc_sample_members += hs.all_members;
+    c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : (1u << 22);
+    if (c->segs.size() > 48) TRY(merge_segments(c));
+    *progress = true;
+    return IMM_OK;
+}
+
+// Generate_RRRsets: extend the stream to theta sets (solo path).
+int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
+{
+    TRY(begin_stream(c, theta, seed));
+    while (c->nsets < theta) {
+        TRY(batch_phase1(c, theta));
+        CK(cudaStreamSynchronize(c->stream));
+        TRY(batch_phase2(c));
+        CK(cudaStreamSynchronize(c->stream));
+        bool progress = false;
+        TRY(batch_phase3(c, &progress));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    take_index_time(c);
+    return IMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Find_Most_Influential_Set: buffers and state (prepare), one launch, and
+// the read-back of seeds and per-round coverage (collect).
+// ---------------------------------------------------------------------------
+int select_prepare(imm_ctx* c, uint32_t k, SelectState* out)
 {
     if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
     if (k == 0 || k > c->n) return set_err(c, IMM_EINVAL, "k must be in [1, n]");
-    if (!seeds_out) return set_err(c, IMM_EINVAL, "seeds_out is NULL");
     const uint64_t R = c->nsets;
     TRY(ensure(c, c->work, (size_t)c->n * 4));
     TRY(ensure(c, c->picked, (size_t)c->n));
@@ -600,24 +681,20 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     TRY(ensure(c, c->ubmp_n, (size_t)k * 8));
     TRY(ensure(c, c->seeds, (size_t)k * 4));
     std::vector<DevSegment> hsegs;
-    for (auto& s : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(s.voff), P<uint32_t>(s.inv)});
+    for (auto& sg : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(sg.voff), P<uint32_t>(sg.inv)});
     TRY(ensure(c, c->dsegs, std::max<size_t>(hsegs.size(), 1) * sizeof(DevSegment)));
 
-    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(cudaEventRecord(c->ev[4], c->stream));
     if (!hsegs.empty())
         CK(cudaMemcpyAsync(c->dsegs.p, hsegs.data(), hsegs.size() * sizeof(DevSegment), cudaMemcpyHostToDevice,
                            c->stream));
     CK(cudaMemcpyAsync(c->work.p, c->cnt.p, (size_t)c->n * 4, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(c->picked.p, 0, (size_t)c->n, c->stream));
     if (R) CK(cudaMemsetAsync(c->covered.p, 0, R, c->stream));
-    CK(cudaMemsetAsync(c->keys.p, 0, (size_t)k * 8, c->stream));
-    CK(cudaMemsetAsync(c->newly_n.p, 0, (size_t)k * 8, c->stream));
-    CK(cudaMemsetAsync(c->vol_cov.p, 0, (size_t)k * 8, c->stream));
-    CK(cudaMemsetAsync(c->vol_list.p, 0, (size_t)k * 8, c->stream));
-    CK(cudaMemsetAsync(c->bmp_cov.p, 0, (size_t)k * 8, c->stream));
-    CK(cudaMemsetAsync(c->ubmp_n.p, 0, (size_t)k * 8, c->stream));
+    DBuf* zero_k[] = {&c->keys, &c->newly_n, &c->vol_cov, &c->vol_list, &c->bmp_cov, &c->ubmp_n};
+    for (DBuf* z : zero_k) CK(cudaMemsetAsync(z->p, 0, (size_t)k * 8, c->stream));
 
-    SelectState s;
+    SelectState& s = *out;
     s.n = c->n;
     s.words = (uint32_t)(((uint64_t)c->n + 31) / 32);
     s.nsets = R;
@@ -644,54 +721,348 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
+    return IMM_OK;
+}
+
+// enqueue the read-back of seeds and per-round coverage on `st`
+int select_readback(imm_ctx* c, uint32_t k, cudaStream_t st)
+{
+    if (c->pin_k < k) {
+        if (c->pin_seeds) cudaFreeHost(c->pin_seeds);
+        if (c->pin_newly) cudaFreeHost(c->pin_newly);
+        c->pin_seeds = nullptr;
+        c->pin_newly = nullptr;
+        c->pin_k = 0;
+        CK(cudaMallocHost(&c->pin_seeds, (size_t)k * 4));
+        CK(cudaMallocHost(&c->pin_newly, (size_t)k * 8));
+        c->pin_k = k;
+    }
+    CK(cudaMemcpyAsync(c->pin_seeds, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->pin_newly, c->newly_n.p, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
+    return IMM_OK;
+}
+
+uint64_t select_covered(imm_ctx* c, uint32_t k, uint32_t* seeds_out)
+{
+    uint64_t cov = 0;
+    for (uint32_t j = 0; j < k; ++j) cov += c->pin_newly[j];
+    if (seeds_out) std::memcpy(seeds_out, c->pin_seeds, (size_t)k * 4);
+    return cov;
+}
+
+int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
+{
+    if (!seeds_out) return set_err(c, IMM_EINVAL, "seeds_out is NULL");
+    SelectState s;
+    TRY(select_prepare(c, k, &s));
     // all k rounds in one launch: one CTA for small graphs (block barriers),
     // the whole cooperative grid otherwise; per-round launches if the device
     // refuses a cooperative grid of that size
     if (c->n <= kSelectCtaMaxN) {
         TRY(ensure(c, c->dstate, sizeof(SelectState) + 16));
-        CK(cudaMemcpyAsync(c->dstate.p, &s, sizeof(SelectState), cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(reinterpret_cast<char*>(c->dstate.p) + sizeof(SelectState), &k, 4,
-                           cudaMemcpyHostToDevice, c->stream));
-        CK(launch_select_batch(P<SelectState>(c->dstate),
-                               reinterpret_cast<const uint32_t*>(reinterpret_cast<char*>(c->dstate.p) +
-                                                                 sizeof(SelectState)),
-                               1, c->di, c->stream));
+        c->pin->k = k;
+        c->pin->state = s;
+        CK(cudaMemcpyAsync(c->dstate.p, &c->pin->state, sizeof(SelectState), cudaMemcpyHostToDevice, c->stream));
+        uint32_t* dk = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(c->dstate.p) + sizeof(SelectState));
+        CK(cudaMemcpyAsync(dk, &c->pin->k, 4, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_select_batch(P<SelectState>(c->dstate), dk, 1, c->di, c->stream));
         c->acc_launches += 1;
-        CK(cudaEventRecord(c->ev[1], c->stream));
-        std::vector<unsigned long long> nn0(k);
-        CK(cudaMemcpyAsync(seeds_out, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(nn0.data(), c->newly_n.p, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        c->acc_select_ms += elapsed(c, 0, 1);
-        uint64_t cov0 = 0;
-        for (uint32_t j = 0; j < k; ++j) cov0 += nn0[j];
-        if (covered_out) *covered_out = cov0;
-        return IMM_OK;
-    }
-    const cudaError_t ce = launch_select_all(s, k, c->di, c->stream);
-    if (ce == cudaErrorCooperativeLaunchTooLarge || ce == cudaErrorNotSupported) {
-        cudaGetLastError();
-        for (uint32_t j = 0; j < k; ++j) CK(launch_select_round(s, j, c->di, c->stream, &c->acc_launches));
     } else {
-        CK(ce);
-        c->acc_launches += 1;
+        const cudaError_t ce = launch_select_all(s, k, c->di, c->stream);
+        if (ce == cudaErrorCooperativeLaunchTooLarge || ce == cudaErrorNotSupported) {
+            cudaGetLastError();
+            for (uint32_t j = 0; j < k; ++j) CK(launch_select_round(s, j, c->di, c->stream, &c->acc_launches));
+        } else {
+            CK(ce);
+            c->acc_launches += 1;
+        }
     }
-    CK(cudaEventRecord(c->ev[1], c->stream));
-    std::vector<unsigned long long> nn(k);
-    CK(cudaMemcpyAsync(seeds_out, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(nn.data(), c->newly_n.p, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->ev[5], c->stream));
+    TRY(select_readback(c, k, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->acc_select_ms += elapsed(c, 0, 1);
-    uint64_t cov = 0;
-    for (uint32_t j = 0; j < k; ++j) cov += nn[j];
+    c->acc_select_ms += elapsed(c, 4, 5);
+    const uint64_t cov = select_covered(c, k, seeds_out);
     if (covered_out) *covered_out = cov;
     return IMM_OK;
+}
+
+// Theta_Estimation constants (Tang et al.), same operation order as any plain
+// fp64 evaluation of the formulas; shared by imm_run and the batch engine so
+// both produce bit-identical ladders.
+struct ThetaPlan {
+    double nd, ln_n, lam_p, lam_s, eps_p;
+    uint32_t rounds;
+};
+
+ThetaPlan theta_plan(uint32_t n, uint32_t k, double epsilon, double ell)
+{
+    ThetaPlan p;
+    p.nd = (double)n;
+    p.ln_n = std::log(p.nd);
+    const double ell_p = ell * (1.0 + std::log(2.0) / p.ln_n);
+    p.eps_p = std::sqrt(2.0) * epsilon;
+    double lnC = 0.0;
+    for (uint32_t i = 1; i <= k; i++) lnC += std::log((double)(n - k + i)) - std::log((double)i);
+    p.lam_p = (2.0 + 2.0 * p.eps_p / 3.0) * (lnC + ell_p * p.ln_n + std::log(std::log2(p.nd))) * p.nd /
+              (p.eps_p * p.eps_p);
+    const double g = 1.0 - 1.0 / kE;
+    const double alpha = std::sqrt(ell_p * p.ln_n + std::log(2.0));
+    const double beta = std::sqrt(g * (lnC + ell_p * p.ln_n + std::log(2.0)));
+    const double t = g * alpha + beta;
+    p.lam_s = 2.0 * p.nd * t * t / (epsilon * epsilon);
+    uint32_t lg = 0;
+    while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)n) lg++;
+    p.rounds = lg >= 1 ? lg - 1 : 0;
+    return p;
 }
 
 void reset_acc(imm_ctx* c)
 {
     c->acc_sample_ms = c->acc_select_ms = c->acc_index_ms = 0;
     c->acc_sample_launches = c->acc_launches = c->acc_edges = c->acc_sample_members = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Batch engine: many IMM queries advance together in waves.  Each query runs
+// on a worker context that borrows its graph's device arrays and owns its
+// stream and RRR-set state.  A wave runs one sampling batch of every query
+// still sampling (phases 1-3 for all of them, one host drain per phase) and
+// then one selection launch covering every query that reached its target
+// (one CTA per query).  Every query executes exactly the solo path's steps,
+// so its result is the same as imm_run's on the same inputs.
+// ---------------------------------------------------------------------------
+int make_worker(imm_ctx* g, imm_ctx** out)
+{
+    *out = nullptr;
+    imm_ctx* w = new imm_ctx();
+    w->device = g->device;
+    w->di = g->di;
+    w->alloc = g->alloc;
+    w->has_alloc = g->has_alloc;
+    if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete w;
+        return set_err(g, IMM_ECUDA, "stream creation failed");
+    }
+    w->own_stream = true;
+    bool ok = cudaMallocHost(&w->pin, sizeof(imm_ctx::Pinned)) == cudaSuccess;
+    for (auto& e : w->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        *out = w;  // caller destroys
+        return set_err(g, IMM_ECUDA, "event or pinned allocation failed");
+    }
+    w->n = g->n;
+    w->m = g->m;
+    w->model = g->model;
+    w->row = g->row;
+    w->src = g->src;
+    w->thr = g->thr;
+    w->guide = g->guide;
+    w->borrowed = true;
+    w->arena_limit = g->arena_limit;
+    *out = w;
+    int rc = dalloc(w, w->cnt, (size_t)w->n * 4);
+    if (rc == IMM_OK) rc = dalloc(w, w->cnt_list, (size_t)w->n * 4);
+    if (rc == IMM_OK) rc = dalloc(w, w->off, 8 * 1024);
+    if (rc == IMM_OK) rc = dalloc(w, w->set_bmp, 4 * 1024);
+    if (rc != IMM_OK) return set_err(g, rc, "worker allocation failed: %s", w->err.c_str());
+    w->off_cap = 1023;
+    cudaMemsetAsync(w->cnt.p, 0, (size_t)w->n * 4, w->stream);
+    cudaMemsetAsync(w->cnt_list.p, 0, (size_t)w->n * 4, w->stream);
+    cudaMemsetAsync(w->off.p, 0, 8, w->stream);
+    w->loaded = true;
+    return IMM_OK;
+}
+
+void destroy_worker(imm_ctx* w);
+
+struct Job {
+    imm_ctx* w = nullptr;
+    uint32_t k = 0;
+    double eps = 0, ell = 0;
+    uint64_t seed = 0;
+    ThetaPlan plan{};
+    double lb = 1.0;
+    uint32_t i = 1;
+    int stage = 0;  // 0 sample round i, 1 select round i, 2 sample final, 3 select final, 4 done, 5 failed
+    uint64_t target = 0;
+    imm_stats st{};
+    int status = IMM_OK;
+    std::string err;
+    std::chrono::steady_clock::time_point t0;
+    uint32_t* seeds_out = nullptr;  // host, k entries
+};
+
+void job_fail(Job& j, int rc)
+{
+    j.status = rc;
+    j.err = j.w ? j.w->err : std::string("no worker");
+    j.stage = 5;
+}
+
+int job_final_target(Job& j)
+{
+    const double tf = std::ceil(j.plan.lam_s / j.lb);
+    if (tf >= 4294967295.0) return set_err(j.w, IMM_EINVAL, "theta exceeds 2^32-2");
+    j.st.lb = j.lb;
+    j.st.theta = (uint64_t)tf;
+    j.target = std::max<uint64_t>(j.st.theta, j.w->nsets);
+    j.stage = 2;
+    return IMM_OK;
+}
+
+int job_round_target(Job& j)
+{
+    const double x = std::ldexp(j.plan.nd, -(int)j.i);
+    const double th = std::ceil(j.plan.lam_p / x);
+    if (th >= 4294967295.0) return set_err(j.w, IMM_EINVAL, "theta_%u exceeds 2^32-2", j.i);
+    j.target = (uint64_t)th;
+    j.stage = 0;
+    return IMM_OK;
+}
+
+int job_start(Job& j)
+{
+    imm_ctx* w = j.w;
+    j.t0 = std::chrono::steady_clock::now();
+    drop_stream(w);
+    reset_acc(w);
+    std::memset(&j.st, 0, sizeof(j.st));
+    j.plan = theta_plan(w->n, j.k, j.eps, j.ell);
+    j.st.lambda_prime = j.plan.lam_p;
+    j.st.lambda_star = j.plan.lam_s;
+    j.lb = 1.0;
+    j.i = 1;
+    TRY(j.plan.rounds >= 1 ? job_round_target(j) : job_final_target(j));
+    return begin_stream(w, j.target, j.seed);
+}
+
+int job_after_select(Job& j, uint64_t cov)
+{
+    imm_ctx* w = j.w;
+    if (j.stage == 1) {
+        const double x = std::ldexp(j.plan.nd, -(int)j.i);
+        const double nF = j.plan.nd * (double)cov / (double)w->nsets;
+        if (j.i - 1 < IMM_MAX_ROUNDS) {
+            j.st.theta_i[j.i - 1] = j.target;
+            j.st.covered_i[j.i - 1] = cov;
+            j.st.sets_i[j.i - 1] = w->nsets;
+        }
+        j.st.rounds = j.i;
+        if (nF >= (1.0 + j.plan.eps_p) * x) {
+            j.lb = nF / (1.0 + j.plan.eps_p);
+            j.st.stopped_early = 1;
+            return job_final_target(j);
+        }
+        if (j.i < j.plan.rounds) {
+            ++j.i;
+            return job_round_target(j);
+        }
+        return job_final_target(j);
+    }
+    // final selection
+    std::memcpy(j.seeds_out, w->pin_seeds, (size_t)j.k * 4);
+    j.st.num_sets = w->nsets;
+    j.st.covered = cov;
+    j.st.members = w->nmembers;
+    j.st.edges_examined = w->acc_edges;
+    j.st.ms_sample = w->acc_sample_ms;
+    j.st.ms_select = w->acc_select_ms;
+    j.st.ms_index = w->acc_index_ms;
+    j.st.sample_launches = w->acc_sample_launches;
+    j.st.kernel_launches = w->acc_launches;
+    j.st.sample_edges = w->acc_edges;
+    j.st.sample_members = w->acc_sample_members;
+    j.st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - j.t0).count();
+    j.stage = 4;
+    return IMM_OK;
+}
+
+// One wave over the active jobs.  `master` is the stream of the selection
+// launch; `host` is the context that owns the device copy of the states.
+int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64_t* launches)
+{
+    std::vector<Job*> S;
+    for (Job* j : jobs) {
+        if (j->stage != 0 && j->stage != 2) continue;
+        if (j->w->nsets >= j->target) {
+            ++j->stage;
+            continue;
+        }
+        S.push_back(j);
+    }
+    for (Job* j : S) {
+        int rc = batch_phase1(j->w, j->target);
+        if (rc != IMM_OK) job_fail(*j, rc);
+    }
+    for (Job* j : S) {
+        if (j->stage == 5) continue;
+        int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+        if (rc == IMM_OK) rc = batch_phase2(j->w);
+        if (rc != IMM_OK) job_fail(*j, rc);
+    }
+    for (Job* j : S) {
+        if (j->stage == 5) continue;
+        bool progress = false;
+        int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+        if (rc == IMM_OK) rc = batch_phase3(j->w, &progress);
+        if (rc != IMM_OK) job_fail(*j, rc);
+        else if (j->w->nsets >= j->target) ++j->stage;
+    }
+    std::vector<Job*> L;
+    for (Job* j : jobs)
+        if (j->stage == 1 || j->stage == 3) L.push_back(j);
+    if (L.empty()) return IMM_OK;
+    // selection: prepare each job's state on its stream, one launch for all
+    const size_t rec = sizeof(SelectState);
+    std::vector<SelectState> states(L.size());
+    std::vector<uint32_t> ks(L.size());
+    std::vector<Job*> ok;
+    for (size_t t = 0; t < L.size(); ++t) {
+        Job* j = L[t];
+        int rc = select_prepare(j->w, j->k, &states[ok.size()]);
+        if (rc != IMM_OK) {
+            job_fail(*j, rc);
+            continue;
+        }
+        ks[ok.size()] = j->k;
+        cudaEventRecord(j->w->ev[4], j->w->stream);
+        cudaStreamWaitEvent(master, j->w->ev[4], 0);
+        ok.push_back(j);
+    }
+    if (ok.empty()) return IMM_OK;
+    const size_t nbytes = ok.size() * (rec + 4) + 16;
+    TRY(ensure(host, host->bstates, nbytes));
+    // the states are staged through pinned memory owned by the engine call
+    void* hbuf = nullptr;
+    if (cudaMallocHost(&hbuf, nbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(host, IMM_ECUDA, "pinned staging allocation failed");
+    }
+    std::memcpy(hbuf, states.data(), ok.size() * rec);
+    std::memcpy(static_cast<char*>(hbuf) + ok.size() * rec, ks.data(), ok.size() * 4);
+    cudaError_t e = cudaMemcpyAsync(host->bstates.p, hbuf, ok.size() * (rec + 4), cudaMemcpyHostToDevice, master);
+    if (e == cudaSuccess)
+        e = launch_select_batch(P<SelectState>(host->bstates),
+                                reinterpret_cast<const uint32_t*>(static_cast<char*>(host->bstates.p) + ok.size() * rec),
+                                (uint32_t)ok.size(), host->di, master);
+    if (launches) *launches += 1;
+    for (Job* j : ok) {
+        if (e != cudaSuccess) break;
+        j->w->acc_launches += 1;
+        if (select_readback(j->w, j->k, master) != IMM_OK) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(master);
+    cudaFreeHost(hbuf);
+    if (e != cudaSuccess) return cuda_err(host, e, "batched selection");
+    for (Job* j : ok) {
+        const uint64_t cov = select_covered(j->w, j->k, nullptr);
+        int rc = job_after_select(*j, cov);
+        if (rc == IMM_OK && (j->stage == 0 || j->stage == 2)) rc = begin_stream(j->w, j->target, j->seed);
+        if (rc != IMM_OK) job_fail(*j, rc);
+    }
+    return IMM_OK;
 }
 
 }  // namespace
@@ -731,6 +1102,11 @@ int imm_create(imm_ctx** out, int device, const imm_alloc* alloc, void* stream)
             return IMM_ECUDA;
         }
     }
+    if (cudaMallocHost(&c->pin, sizeof(imm_ctx::Pinned)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return IMM_ECUDA;
+    }
     *out = c;
     return IMM_OK;
 }
@@ -750,6 +1126,9 @@ void imm_destroy(imm_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->pin) cudaFreeHost(c->pin);
+    if (c->pin_seeds) cudaFreeHost(c->pin_seeds);
+    if (c->pin_newly) cudaFreeHost(c->pin_newly);
     delete c;
 }
 
@@ -830,24 +1209,9 @@ int imm_run(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint6
     imm_stats st;
     std::memset(&st, 0, sizeof(st));
 
-    // Theta_Estimation constants (Tang et al.), same operation order as any
-    // plain fp64 evaluation of the formulas.
-    const double nd = (double)c->n;
-    const double ln_n = std::log(nd);
-    const double ell_p = ell * (1.0 + std::log(2.0) / ln_n);
-    const double eps_p = std::sqrt(2.0) * epsilon;
-    double lnC = 0.0;
-    for (uint32_t i = 1; i <= k; i++) lnC += std::log((double)(c->n - k + i)) - std::log((double)i);
-    const double lam_p =
-        (2.0 + 2.0 * eps_p / 3.0) * (lnC + ell_p * ln_n + std::log(std::log2(nd))) * nd / (eps_p * eps_p);
-    const double g = 1.0 - 1.0 / kE;
-    const double alpha = std::sqrt(ell_p * ln_n + std::log(2.0));
-    const double beta = std::sqrt(g * (lnC + ell_p * ln_n + std::log(2.0)));
-    const double t = g * alpha + beta;
-    const double lam_s = 2.0 * nd * t * t / (epsilon * epsilon);
-    uint32_t lg = 0;
-    while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)c->n) lg++;
-    const uint32_t rounds = lg >= 1 ? lg - 1 : 0;
+    const ThetaPlan tp = theta_plan(c->n, k, epsilon, ell);
+    const double nd = tp.nd, lam_p = tp.lam_p, lam_s = tp.lam_s, eps_p = tp.eps_p;
+    const uint32_t rounds = tp.rounds;
     st.lambda_prime = lam_p;
     st.lambda_star = lam_s;
 
@@ -999,3 +1363,62 @@ int imm_get_counts(imm_ctx* c, uint32_t* cnt_out)
 }
 
 }  // extern "C"
+
+namespace {
+void destroy_worker(imm_ctx* w)
+{
+    if (!w) return;
+    cudaStream_t st = w->own_stream ? w->stream : nullptr;
+    imm_destroy(w);
+    if (st) cudaStreamDestroy(st);
+}
+}  // namespace
+
+extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* seeds_out, imm_stats* stats_out,
+                             int* status_out)
+{
+    if (nq == 0) return IMM_OK;
+    if (!queries || !seeds_out) return IMM_EINVAL;
+    imm_ctx* g0 = queries[0].graph;
+    if (!g0) return IMM_EINVAL;
+    DeviceGuard guard(g0->device);
+    for (uint32_t q = 0; q < nq; ++q) {
+        const imm_query& Q = queries[q];
+        if (!Q.graph || !Q.graph->loaded || Q.graph->device != g0->device)
+            return set_err(g0, IMM_EINVAL, "query %u: graph context missing, not loaded or on another device", q);
+        if (Q.k == 0 || Q.k > Q.graph->n || !(Q.epsilon > 0.0 && Q.epsilon < 1.0) || !(Q.ell > 0.0))
+            return set_err(g0, IMM_EINVAL, "query %u: bad k, epsilon or ell", q);
+    }
+    std::vector<Job> jobs(nq);
+    std::vector<Job*> active;
+    uint64_t off = 0;
+    int rc = IMM_OK;
+    for (uint32_t q = 0; q < nq; ++q) {
+        Job& j = jobs[q];
+        j.k = queries[q].k;
+        j.eps = queries[q].epsilon;
+        j.ell = queries[q].ell;
+        j.seed = queries[q].rng_seed;
+        j.seeds_out = seeds_out + off;
+        off += j.k;
+        rc = make_worker(queries[q].graph, &j.w);
+        if (rc != IMM_OK) break;
+        rc = job_start(j);
+        if (rc != IMM_OK) job_fail(j, rc);
+        active.push_back(&j);
+        rc = IMM_OK;
+    }
+    uint64_t launches = 0;
+    while (rc == IMM_OK) {
+        bool any = false;
+        for (Job* j : active) any = any || (j->stage < 4);
+        if (!any) break;
+        rc = run_wave(active, g0, g0->stream, &launches);
+    }
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (status_out) status_out[q] = jobs[q].stage == 4 ? IMM_OK : (jobs[q].status ? jobs[q].status : rc);
+        if (stats_out) stats_out[q] = jobs[q].st;
+        destroy_worker(jobs[q].w);
+    }
+    return rc;
+}

@@ -62,6 +62,11 @@ class imm_stats(ctypes.Structure):
         return d
 
 
+class imm_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("k", ctypes.c_uint32), ("epsilon", ctypes.c_double),
+                ("ell", ctypes.c_double), ("rng_seed", ctypes.c_uint64)]
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -103,6 +108,7 @@ def _load():
         "imm_get_counts": ([vp, vp], i32),
         "imm_set_arena_limit": ([vp, u64], i32),
         "imm_select_noalloc": ([u32, u64, vp, vp, u32, vp, vp, vp], i32),
+        "imm_run_batch": ([ctypes.POINTER(imm_query), u32, vp, ctypes.POINTER(imm_stats), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +221,29 @@ def imm_run(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_seed:
     st = imm_stats()
     _check(ctx, _load().imm_run(ctx.handle, model, k, epsilon, ell, rng_seed, seeds.ctypes.data, ctypes.byref(st)))
     return seeds[:k], st
+
+
+def imm_run_batch(queries):
+    """queries: list of (graph_ctx, k, epsilon, ell, rng_seed).  Returns
+    (seeds per query, imm_stats per query, status per query); raises ImmError
+    only when the batch as a whole is rejected."""
+    nq = len(queries)
+    arr = (imm_query * max(nq, 1))()
+    total = 0
+    for i, (g, k, eps, ell, seed) in enumerate(queries):
+        arr[i] = imm_query(g.handle, k, eps, ell, seed)
+        total += k
+    seeds = np.zeros(max(total, 1), dtype=np.uint32)
+    stats = (imm_stats * max(nq, 1))()
+    status = np.zeros(max(nq, 1), dtype=np.int32)
+    rc = _load().imm_run_batch(arr, nq, seeds.ctypes.data, stats, status.ctypes.data)
+    if rc != IMM_OK:
+        _check(queries[0][0] if nq else None, rc)
+    out, off = [], 0
+    for (_, k, _, _, _) in queries:
+        out.append(seeds[off:off + k].copy())
+        off += k
+    return out, [stats[i] for i in range(nq)], [int(x) for x in status[:nq]]
 
 
 def imm_reset_sets(ctx: _Ctx) -> None:
