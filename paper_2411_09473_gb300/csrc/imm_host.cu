@@ -359,6 +359,9 @@ int load_graph_common(imm_ctx* c, uint32_t n, uint64_t m, const void* row, const
     TRY(dalloc(c, c->set_bmp, 4 * 1024));
     c->off_cap = 1023;
     CK(cudaMemsetAsync(c->off.p, 0, 8, c->stream));
+    // the graph is complete before the call returns: contexts that borrow it
+    // run on other streams
+    CK(cudaStreamSynchronize(c->stream));
     c->loaded = true;
     return IMM_OK;
 }
@@ -1388,6 +1391,11 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
             return set_err(g0, IMM_EINVAL, "query %u: graph context missing, not loaded or on another device", q);
         if (Q.k == 0 || Q.k > Q.graph->n || !(Q.epsilon > 0.0 && Q.epsilon < 1.0) || !(Q.ell > 0.0))
             return set_err(g0, IMM_EINVAL, "query %u: bad k, epsilon or ell", q);
+    }
+    // every graph finished loading before any worker stream reads it
+    for (uint32_t q = 0; q < nq; ++q) {
+        const cudaError_t e = cudaStreamSynchronize(queries[q].graph->stream);
+        if (e != cudaSuccess) return cuda_err(g0, e, "graph stream");
     }
     std::vector<Job> jobs(nq);
     std::vector<Job*> active;
