@@ -142,8 +142,11 @@ def _torch_allocator(device: int, stream_int: int):
     import torch
 
     def _alloc(user, nbytes, stream):
+        # The block belongs to the stream the library names (a batch worker's
+        # own stream, not the creating context's): torch's caching allocator
+        # only reuses a freed block in that stream's order.
         try:
-            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=stream_int)
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=int(stream or 0))
         except Exception:
             return None
 
