@@ -37,7 +37,7 @@ METRIC = "IMM seconds-to-seeds"
 # (profiles/ic_large_kernel__ic_u01_1m_first2000sets.md: 12.454 GB over
 # 4,620,412,076 in-edges).  Traffic of a full launch is scaled by its in-edges.
 IC_LARGE_DRAM_BYTES_PER_EDGE = 12.454e9 / 4620412076
-WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "batch64")
+WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "batch64", "served")
 
 
 def parse():
@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--served-queries", type=int, default=10000)
+    ap.add_argument("--served-rate", type=float, default=200.0)
+    ap.add_argument("--served-solo", type=int, default=200, help="queries timed one at a time for comparison")
     return ap.parse_args()
 
 
@@ -460,6 +463,95 @@ def run_batch(args, dist: Dist):
         print(json.dumps(line), flush=True)
 
 
+def run_served(args, dist: Dist):
+    """Served IMM: 8 resident R-MAT graphs (n log-spaced 2^16..2^20, average
+    degree 16, IC/LT alternating, w = 1/indeg), a Poisson stream of queries
+    (rate --served-rate, k = U{10..200}, eps = U(0.1, 0.5), graph uniform),
+    replayed in real time against imm_server; latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_2411_09473_gb300 import imm
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    graphs = graphgen.served_graphs()
+    ctxs = []
+    for g in graphs:
+        c = imm.imm_create(device=dev, stream=stream)
+        imm.imm_load_graph(c, g.n, g.m, g.row, g.src, g.weight, g.model)
+        ctxs.append(c)
+    qs = graphgen.served_queries(count=args.served_queries, rate_per_s=args.served_rate, num_graphs=len(graphs))
+    srv = imm.imm_server_create(ctxs, memory_budget_bytes=96 << 30, max_active=192)
+    # warm-up: a few queries through the server
+    for q in qs[:max(args.warmup, 1) * 4]:
+        imm.imm_server_submit(srv, q.graph_id, q.k, q.epsilon, q.ell, 10 ** 9 + q.seed)
+    got = 0
+    while got < max(args.warmup, 1) * 4:
+        for (qid, status, _, _) in imm.imm_server_poll(srv):
+            imm.imm_server_take(srv, qid, 256)
+            got += 1
+        time.sleep(0.001)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ids, lat, failed = {}, {}, 0
+    keep = {}
+    t0 = time.perf_counter()
+    i, n = 0, len(qs)
+    while len(lat) + failed < n:
+        now = time.perf_counter() - t0
+        while i < n and qs[i].arrival_s <= now:
+            q = qs[i]
+            ids[imm.imm_server_submit(srv, q.graph_id, q.k, q.epsilon, q.ell, q.seed)] = i
+            i += 1
+        for (qid, status, latency_ms, queue_ms) in imm.imm_server_poll(srv):
+            j = ids[qid]
+            if status != 0:
+                failed += 1
+                continue
+            # latency from the scheduled arrival (submission can lag it slightly)
+            lat[j] = (time.perf_counter() - t0 - qs[j].arrival_s) * 1e3
+            seeds, st = imm.imm_server_take(srv, qid, qs[j].k)
+            if j < 20:
+                keep[j] = seeds
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    info = imm.imm_server_info(srv)
+    imm.imm_server_destroy(srv)
+    # one at a time on the same contexts: capacity of the plain path
+    m = min(args.served_solo, n)
+    torch.cuda.synchronize()
+    ts = time.perf_counter()
+    for j in range(m):
+        q = qs[j]
+        s2, _ = imm.imm_run(ctxs[q.graph_id], graphs[q.graph_id].model, q.k, q.epsilon, q.ell, q.seed)
+        if j in keep:
+            assert np.array_equal(s2, keep[j]), j
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - ts
+    lats = np.array([lat[j] for j in sorted(lat)])
+    if dist.rank == 0:
+        line = {
+            "metric": "served IMM queries/s", "value": len(lat) / wall, "unit": "queries/s", "n_gpus": dist.world,
+            "steps": 1, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{n} queries, Poisson {args.served_rate:g}/s, 8 resident R-MAT graphs "
+                                   "2^16..2^20 (avg deg 16, IC/LT alternating, w=1/indeg), k=U{10..200}, "
+                                   "eps=U(0.1,0.5), stream seed 5", "parallelism": f"replicas x{dist.world}"},
+            "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
+                           "max": float(lats.max()), "mean": float(lats.mean())},
+            "offered_rate": args.served_rate, "completed": int(len(lat)), "failed": int(failed),
+            "one_at_a_time": {"value": m / solo_s, "unit": "queries/s", "queries": m,
+                              "results_identical_checked": len([j for j in keep if j < m])},
+            "server": info, "roofline": None, "gpu_launches": None, "clocks": clk, "e2e": None,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -468,6 +560,8 @@ def main():
             run_reference(args, dist)
         elif args.workload == "batch64":
             run_batch(args, dist)
+        elif args.workload == "served":
+            run_served(args, dist)
         else:
             run_gpu(args, dist)
     finally:

@@ -186,6 +186,50 @@ typedef struct imm_query {
 int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* seeds_out, imm_stats* stats_out,
                   int* status_out);
 
+/* ---- served IMM (continuous batching) ----
+ * A server keeps the given graphs resident (caller-owned contexts that must
+ * outlive it) and runs IMM queries on a host thread in waves (as
+ * imm_run_batch).  Between waves it admits submitted queries while fewer
+ * than max_active are in flight and its workers' device memory is under
+ * memory_budget_bytes (0 = no limit; each query's arena is then limited to
+ * half the budget), so queries that arrive while others are on the GPU join
+ * the next wave and overlap with them.  Every result equals the query's solo
+ * imm_run.  Server workers allocate with cudaMallocAsync on their own
+ * streams (never through the contexts' allocator callbacks). */
+typedef struct imm_server imm_server;
+
+typedef struct imm_server_config {
+    uint64_t memory_budget_bytes;
+    uint32_t max_active;  /* 0 = 64 */
+} imm_server_config;
+
+typedef struct imm_completion {
+    uint64_t id;
+    int status;          /* IMM_OK or the query's error */
+    double latency_ms;   /* submission to completion */
+    double queue_ms;     /* submission to admission */
+} imm_completion;
+
+/* Errors: EINVAL (no graphs, a graph not loaded, contexts on different
+ * devices), ECUDA, ENOMEM. */
+int imm_server_create(imm_server** out, imm_ctx* const* graphs, uint32_t ngraphs, const imm_server_config* cfg);
+/* Queue a query on graph index `graph` (position in the create call's list);
+ * *id_out receives its id.  Errors: EINVAL (bad graph index, k, eps, ell),
+ * or the status of a failure that stopped the server. */
+int imm_server_submit(imm_server* s, uint32_t graph, uint32_t k, double epsilon, double ell, uint64_t rng_seed,
+                      uint64_t* id_out);
+/* Non-blocking: up to cap completions (oldest first) into out (host). */
+int imm_server_poll(imm_server* s, imm_completion* out, uint32_t cap, uint32_t* n_out);
+/* Results of a completed query (seeds_out: host, k >= the query's k;
+ * stats_out nullable); the query is then forgotten.  Errors: ESTATE (id not
+ * completed or unknown), EINVAL (k too small), or the query's own error. */
+int imm_server_take(imm_server* s, uint64_t id, uint32_t* seeds_out, uint32_t k, imm_stats* stats_out);
+/* Queue depth, queries in flight, waves run, device bytes held; returns the
+ * status of a failure that stopped the server (IMM_OK if none). */
+int imm_server_info(imm_server* s, uint64_t* pending, uint64_t* active, uint64_t* waves, uint64_t* device_bytes);
+/* Stop the loop (the wave in progress finishes), free everything. */
+void imm_server_destroy(imm_server* s);
+
 /* Drop the RRR-set stream (counts, arena, index); keeps the graph. */
 int imm_reset_sets(imm_ctx* ctx);
 

@@ -7,7 +7,13 @@
 // FMA contraction (-ffp-contract=off), so theta, LB and the ladder are
 // bit-identical to any other IEEE evaluation in the same order.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -94,6 +100,7 @@ struct imm_ctx {
 
     DBuf flags;
     uint64_t arena_limit = 0;
+    uint64_t dev_bytes = 0;  // device bytes this context holds
     uint32_t next_batch = 1u << 22;
     double avg_len = 0.0;
 
@@ -167,6 +174,7 @@ struct DeviceGuard {
 void dfree(imm_ctx* c, DBuf& b)
 {
     if (b.p) {
+        c->dev_bytes -= std::min<uint64_t>(c->dev_bytes, b.bytes);
         if (c->has_alloc) c->alloc.free(c->alloc.user, b.p, b.bytes, c->stream);
         else cudaFreeAsync(b.p, c->stream);
     }
@@ -188,6 +196,7 @@ int dalloc(imm_ctx* c, DBuf& b, size_t bytes)
     if (!p) return set_err(c, IMM_ENOMEM, "device allocation of %zu bytes failed", bytes);
     b.p = p;
     b.bytes = bytes;
+    c->dev_bytes += bytes;
     return IMM_OK;
 }
 
@@ -834,14 +843,14 @@ void reset_acc(imm_ctx* c)
 // (one CTA per query).  Every query executes exactly the solo path's steps,
 // so its result is the same as imm_run's on the same inputs.
 // ---------------------------------------------------------------------------
-int make_worker(imm_ctx* g, imm_ctx** out)
+int make_worker(imm_ctx* g, imm_ctx** out, bool own_allocator = false)
 {
     *out = nullptr;
     imm_ctx* w = new imm_ctx();
     w->device = g->device;
     w->di = g->di;
     w->alloc = g->alloc;
-    w->has_alloc = g->has_alloc;
+    w->has_alloc = g->has_alloc && !own_allocator;
     if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         delete w;
@@ -1430,3 +1439,251 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
     }
     return rc;
 }
+
+// ===========================================================================
+// Served IMM: a continuous-batching loop on a host thread.  Queries are
+// submitted at any time; between waves the loop admits pending queries (up
+// to max_active in flight and while the workers' device memory stays under
+// the budget), runs one wave over every admitted query, and retires the
+// finished ones with their latency.  Admitted queries join the next wave, so
+// newcomers overlap on the GPU with queries already in flight.  Each result
+// equals the query's solo imm_run.  Server workers allocate with the
+// library's own stream-ordered allocator, so the loop thread never calls back
+// into the caller's allocator.
+// ===========================================================================
+namespace {
+
+struct ServedQuery {
+    uint64_t id = 0;
+    uint32_t graph = 0;
+    Job job;
+    std::vector<uint32_t> seeds;
+    std::chrono::steady_clock::time_point submitted, admitted, finished;
+};
+
+}  // namespace
+
+struct imm_server {
+    std::vector<imm_ctx*> graphs;
+    imm_server_config cfg{};
+    imm_ctx* host = nullptr;  // master stream + device copy of selection states
+    std::vector<std::vector<imm_ctx*>> idle;  // per graph: workers ready for reuse
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<ServedQuery*> pending;
+    std::vector<ServedQuery*> active;
+    std::deque<ServedQuery*> done;
+    std::unordered_map<uint64_t, ServedQuery*> finished;
+    std::atomic<bool> stop{false};
+    std::thread loop;
+    uint64_t next_id = 1;
+    uint64_t waves = 0, launches = 0;
+    int fatal = IMM_OK;
+    std::string err;
+};
+
+namespace {
+
+uint64_t active_bytes(imm_server* s)
+{
+    uint64_t b = s->host ? s->host->dev_bytes : 0;
+    for (ServedQuery* q : s->active) b += q->job.w ? q->job.w->dev_bytes : 0;
+    for (auto& v : s->idle)
+        for (imm_ctx* w : v) b += w->dev_bytes;
+    return b;
+}
+
+void server_loop(imm_server* s)
+{
+    DeviceGuard guard(s->host->device);
+    while (!s->stop.load()) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->active.empty() && s->pending.empty())
+                s->cv.wait_for(lk, std::chrono::milliseconds(2));
+            // admission: concurrency and device memory
+            while (!s->pending.empty() && s->active.size() < s->cfg.max_active &&
+                   (s->cfg.memory_budget_bytes == 0 || active_bytes(s) < s->cfg.memory_budget_bytes)) {
+                ServedQuery* q = s->pending.front();
+                s->pending.pop_front();
+                q->admitted = std::chrono::steady_clock::now();
+                imm_ctx* w = nullptr;
+                auto& pool = s->idle[q->graph];
+                int rc = IMM_OK;
+                if (!pool.empty()) {
+                    w = pool.back();
+                    pool.pop_back();
+                } else {
+                    rc = make_worker(s->graphs[q->graph], &w, true);
+                }
+                q->job.w = w;
+                if (rc == IMM_OK && s->cfg.memory_budget_bytes) w->arena_limit = s->cfg.memory_budget_bytes / 2;
+                if (rc == IMM_OK) rc = job_start(q->job);
+                if (rc != IMM_OK) job_fail(q->job, rc);
+                s->active.push_back(q);
+            }
+        }
+        if (s->active.empty()) continue;
+        std::vector<Job*> jobs;
+        for (ServedQuery* q : s->active) jobs.push_back(&q->job);
+        const int rc = run_wave(jobs, s->host, s->host->stream, &s->launches);
+        ++s->waves;
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (rc != IMM_OK) {
+            s->fatal = rc;
+            s->err = s->host->err;
+            for (ServedQuery* q : s->active) {
+                if (q->job.stage < 4) job_fail(q->job, rc);
+            }
+        }
+        std::vector<ServedQuery*> still;
+        for (ServedQuery* q : s->active) {
+            if (q->job.stage >= 4) {
+                q->finished = std::chrono::steady_clock::now();
+                if (q->job.w) {
+                    drop_stream(q->job.w);
+                    cudaStreamSynchronize(q->job.w->stream);
+                    s->idle[q->graph].push_back(q->job.w);
+                    q->job.w = nullptr;
+                }
+                s->done.push_back(q);
+                s->finished[q->id] = q;
+            } else {
+                still.push_back(q);
+            }
+        }
+        s->active.swap(still);
+        if (rc != IMM_OK) break;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int imm_server_create(imm_server** out, imm_ctx* const* graphs, uint32_t ngraphs, const imm_server_config* cfg)
+{
+    if (!out || !graphs || ngraphs == 0) return IMM_EINVAL;
+    *out = nullptr;
+    for (uint32_t i = 0; i < ngraphs; ++i)
+        if (!graphs[i] || !graphs[i]->loaded || graphs[i]->device != graphs[0]->device) return IMM_EINVAL;
+    DeviceGuard guard(graphs[0]->device);
+    for (uint32_t i = 0; i < ngraphs; ++i)
+        if (cudaStreamSynchronize(graphs[i]->stream) != cudaSuccess) return IMM_ECUDA;
+    imm_server* s = new imm_server();
+    s->graphs.assign(graphs, graphs + ngraphs);
+    s->idle.resize(ngraphs);
+    if (cfg) s->cfg = *cfg;
+    if (s->cfg.max_active == 0) s->cfg.max_active = 64;
+    int rc = make_worker(graphs[0], &s->host, true);
+    if (rc != IMM_OK) {
+        destroy_worker(s->host);
+        delete s;
+        return rc;
+    }
+    s->loop = std::thread(server_loop, s);
+    *out = s;
+    return IMM_OK;
+}
+
+int imm_server_submit(imm_server* s, uint32_t graph, uint32_t k, double epsilon, double ell, uint64_t rng_seed,
+                      uint64_t* id_out)
+{
+    if (!s || graph >= s->graphs.size()) return IMM_EINVAL;
+    imm_ctx* g = s->graphs[graph];
+    if (k == 0 || k > g->n || !(epsilon > 0.0 && epsilon < 1.0) || !(ell > 0.0)) return IMM_EINVAL;
+    ServedQuery* q = new ServedQuery();
+    q->graph = graph;
+    q->job.k = k;
+    q->job.eps = epsilon;
+    q->job.ell = ell;
+    q->job.seed = rng_seed;
+    q->seeds.assign(k, 0);
+    q->job.seeds_out = q->seeds.data();
+    q->submitted = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->fatal != IMM_OK) {
+            delete q;
+            return s->fatal;
+        }
+        q->id = s->next_id++;
+        s->pending.push_back(q);
+    }
+    s->cv.notify_one();
+    if (id_out) *id_out = q->id;
+    return IMM_OK;
+}
+
+int imm_server_poll(imm_server* s, imm_completion* out, uint32_t cap, uint32_t* n_out)
+{
+    if (!s || !n_out || (cap && !out)) return IMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    uint32_t n = 0;
+    while (n < cap && !s->done.empty()) {
+        ServedQuery* q = s->done.front();
+        s->done.pop_front();
+        imm_completion& c = out[n++];
+        c.id = q->id;
+        c.status = q->job.stage == 4 ? IMM_OK : (q->job.status ? q->job.status : IMM_ECUDA);
+        c.latency_ms = std::chrono::duration<double, std::milli>(q->finished - q->submitted).count();
+        c.queue_ms = std::chrono::duration<double, std::milli>(q->admitted - q->submitted).count();
+    }
+    *n_out = n;
+    return IMM_OK;
+}
+
+int imm_server_take(imm_server* s, uint64_t id, uint32_t* seeds_out, uint32_t k, imm_stats* stats_out)
+{
+    if (!s) return IMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->finished.find(id);
+    if (it == s->finished.end()) return IMM_ESTATE;
+    ServedQuery* q = it->second;
+    if (q->job.stage != 4) {
+        const int st = q->job.status ? q->job.status : IMM_ECUDA;
+        s->finished.erase(it);
+        delete q;
+        return st;
+    }
+    if (seeds_out) {
+        if (k < q->job.k) return IMM_EINVAL;
+        std::memcpy(seeds_out, q->seeds.data(), (size_t)q->job.k * 4);
+    }
+    if (stats_out) *stats_out = q->job.st;
+    s->finished.erase(it);
+    delete q;
+    return IMM_OK;
+}
+
+int imm_server_info(imm_server* s, uint64_t* pending, uint64_t* active, uint64_t* waves, uint64_t* device_bytes)
+{
+    if (!s) return IMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (pending) *pending = s->pending.size();
+    if (active) *active = s->active.size();
+    if (waves) *waves = s->waves;
+    if (device_bytes) *device_bytes = active_bytes(s);
+    return s->fatal;
+}
+
+void imm_server_destroy(imm_server* s)
+{
+    if (!s) return;
+    s->stop.store(true);
+    s->cv.notify_one();
+    if (s->loop.joinable()) s->loop.join();
+    DeviceGuard guard(s->host->device);
+    for (ServedQuery* q : s->active) {
+        destroy_worker(q->job.w);
+        delete q;
+    }
+    for (ServedQuery* q : s->pending) delete q;
+    for (auto& kv : s->finished) delete kv.second;
+    for (auto& v : s->idle)
+        for (imm_ctx* w : v) destroy_worker(w);
+    destroy_worker(s->host);
+    delete s;
+}
+
+}  // extern "C"

@@ -62,6 +62,15 @@ class imm_stats(ctypes.Structure):
         return d
 
 
+class imm_server_config(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32)]
+
+
+class imm_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double)]
+
+
 class imm_query(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_void_p), ("k", ctypes.c_uint32), ("epsilon", ctypes.c_double),
                 ("ell", ctypes.c_double), ("rng_seed", ctypes.c_uint64)]
@@ -109,6 +118,13 @@ def _load():
         "imm_set_arena_limit": ([vp, u64], i32),
         "imm_select_noalloc": ([u32, u64, vp, vp, u32, vp, vp, vp], i32),
         "imm_run_batch": ([ctypes.POINTER(imm_query), u32, vp, ctypes.POINTER(imm_stats), vp], i32),
+        "imm_server_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), u32, ctypes.POINTER(imm_server_config)], i32),
+        "imm_server_submit": ([vp, u32, u32, f64, f64, u64, ctypes.POINTER(u64)], i32),
+        "imm_server_poll": ([vp, ctypes.POINTER(imm_completion), u32, ctypes.POINTER(u32)], i32),
+        "imm_server_take": ([vp, u64, vp, u32, ctypes.POINTER(imm_stats)], i32),
+        "imm_server_info": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                             ctypes.POINTER(u64)], i32),
+        "imm_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -312,3 +328,67 @@ def imm_select_noalloc(n: int, nsets: int, d_off, d_members, k: int, d_seeds_out
     if rc != IMM_OK:
         raise ImmError(rc, "imm_select_noalloc rejected the call (sizes above the fixed scratch limits, "
                            "bad k, or a NULL pointer)" if rc == IMM_EINVAL else "CUDA error")
+
+
+class _Server:
+    def __init__(self, handle, graphs):
+        self.handle = handle
+        self._graphs = graphs  # keep the graph contexts alive
+
+    def __del__(self):
+        try:
+            imm_server_destroy(self)
+        except Exception:
+            pass
+
+
+def imm_server_create(graphs, memory_budget_bytes: int = 0, max_active: int = 64) -> _Server:
+    """Continuous-batching server over loaded graph contexts (kept alive by the handle)."""
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle.value if hasattr(g.handle, "value") else g.handle
+                                              for g in graphs])
+    cfg = imm_server_config(memory_budget_bytes, max_active)
+    h = ctypes.c_void_p()
+    rc = _load().imm_server_create(ctypes.byref(h), arr, len(graphs), ctypes.byref(cfg))
+    if rc != IMM_OK:
+        raise ImmError(rc, "imm_server_create failed")
+    return _Server(h, list(graphs))
+
+
+def imm_server_submit(server: _Server, graph: int, k: int, epsilon: float, ell: float, rng_seed: int) -> int:
+    qid = ctypes.c_uint64(0)
+    rc = _load().imm_server_submit(server.handle, graph, k, epsilon, ell, rng_seed, ctypes.byref(qid))
+    if rc != IMM_OK:
+        raise ImmError(rc, "imm_server_submit rejected the query")
+    return int(qid.value)
+
+
+def imm_server_poll(server: _Server, cap: int = 1024):
+    buf = (imm_completion * cap)()
+    n = ctypes.c_uint32(0)
+    rc = _load().imm_server_poll(server.handle, buf, cap, ctypes.byref(n))
+    if rc != IMM_OK:
+        raise ImmError(rc, "imm_server_poll failed")
+    return [(int(buf[i].id), int(buf[i].status), float(buf[i].latency_ms), float(buf[i].queue_ms))
+            for i in range(n.value)]
+
+
+def imm_server_take(server: _Server, qid: int, k: int):
+    seeds = np.zeros(max(k, 1), dtype=np.uint32)
+    st = imm_stats()
+    rc = _load().imm_server_take(server.handle, qid, seeds.ctypes.data, k, ctypes.byref(st))
+    if rc != IMM_OK:
+        raise ImmError(rc, f"imm_server_take({qid}) failed")
+    return seeds[:k], st
+
+
+def imm_server_info(server: _Server):
+    a, b, c, d = (ctypes.c_uint64(0) for _ in range(4))
+    rc = _load().imm_server_info(server.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+    return dict(pending=int(a.value), active=int(b.value), waves=int(c.value), device_bytes=int(d.value),
+                status=rc)
+
+
+def imm_server_destroy(server: _Server) -> None:
+    if server.handle:
+        _load().imm_server_destroy(server.handle)
+        server.handle = None

@@ -1,0 +1,73 @@
+"""Served IMM (continuous batching): queries submitted at different times,
+while others are in flight, each return exactly their solo imm_run result."""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def imm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2411_09473_gb300 import imm as mod
+    return mod
+
+
+def load(imm, g):
+    ctx = imm.imm_create(device=0)
+    imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, g.weight, g.model)
+    return ctx
+
+
+def test_served_results_equal_solo_runs(imm):
+    graphs = [graphgen.make_graph(4096, 32768, 1, graphgen.IC, "inv_indeg"),
+              graphgen.make_graph(6000, 60000, 2, graphgen.LT, "inv_indeg"),
+              graphgen.make_graph(20000, 160000, 3, graphgen.IC, "inv_indeg")]
+    ctxs = [load(imm, g) for g in graphs]
+    srv = imm.imm_server_create(ctxs, memory_budget_bytes=8 << 30, max_active=16)
+    rng = np.random.default_rng(0)
+    queries = []
+    for i in range(24):
+        gid = int(rng.integers(0, 3))
+        queries.append((gid, int(rng.integers(1, 40)), float(rng.uniform(0.2, 0.5)), 1.0, 1000 + i))
+    ids = {}
+    for i, q in enumerate(queries):
+        ids[imm.imm_server_submit(srv, *q)] = q
+        if i % 6 == 5:
+            time.sleep(0.02)  # later submissions join waves already in flight
+    got = {}
+    deadline = time.time() + 300
+    while len(got) < len(queries) and time.time() < deadline:
+        for (qid, status, lat, qms) in imm.imm_server_poll(srv):
+            assert status == 0, status
+            assert lat >= qms >= 0
+            q = ids[qid]
+            got[qid] = imm.imm_server_take(srv, qid, q[1])
+        time.sleep(0.005)
+    assert len(got) == len(queries)
+    info = imm.imm_server_info(srv)
+    assert info["status"] == 0 and info["active"] == 0 and info["pending"] == 0
+    imm.imm_server_destroy(srv)
+    for qid, (seeds, st) in got.items():
+        gid, k, eps, ell, seed = ids[qid]
+        s2, st2 = imm.imm_run(ctxs[gid], graphs[gid].model, k, eps, ell, seed)
+        assert np.array_equal(seeds, s2)
+        assert st.theta == st2.theta and st.lb == st2.lb and st.covered == st2.covered
+
+
+def test_served_rejects_bad_queries(imm):
+    g = graphgen.make_graph(1024, 8192, 5, graphgen.IC, "inv_indeg")
+    ctx = load(imm, g)
+    srv = imm.imm_server_create([ctx])
+    with pytest.raises(imm.ImmError):
+        imm.imm_server_submit(srv, 1, 5, 0.5, 1.0, 1)      # no graph 1
+    with pytest.raises(imm.ImmError):
+        imm.imm_server_submit(srv, 0, 0, 0.5, 1.0, 1)      # k = 0
+    with pytest.raises(imm.ImmError):
+        imm.imm_server_take(srv, 12345, 5)                 # unknown id
+    imm.imm_server_destroy(srv)
