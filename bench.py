@@ -484,15 +484,19 @@ def run_served(args, dist: Dist):
         imm.imm_load_graph(c, g.n, g.m, g.row, g.src, g.weight, g.model)
         ctxs.append(c)
     qs = graphgen.served_queries(count=args.served_queries, rate_per_s=args.served_rate, num_graphs=len(graphs))
-    srv = imm.imm_server_create(ctxs, memory_budget_bytes=96 << 30, max_active=192)
+    srv = imm.imm_server_create(ctxs, memory_budget_bytes=96 << 30, max_active=128)
     # warm-up: a few queries through the server
     for q in qs[:max(args.warmup, 1) * 4]:
         imm.imm_server_submit(srv, q.graph_id, q.k, q.epsilon, q.ell, 10 ** 9 + q.seed)
     got = 0
+    t_w = time.perf_counter()
     while got < max(args.warmup, 1) * 4:
         for (qid, status, _, _) in imm.imm_server_poll(srv):
-            imm.imm_server_take(srv, qid, 256)
+            if status == 0:
+                imm.imm_server_take(srv, qid, 256)
             got += 1
+        if time.perf_counter() - t_w > 120:
+            raise RuntimeError(f"served warm-up did not complete: {imm.imm_server_info(srv)}")
         time.sleep(0.001)
     clocks = ClockSampler(dev)
     clocks.start()
@@ -500,8 +504,16 @@ def run_served(args, dist: Dist):
     keep = {}
     t0 = time.perf_counter()
     i, n = 0, len(qs)
+    limit_s = max(60.0, 4.0 * qs[-1].arrival_s)  # the run reports what completed by then
+    last_note = 0.0
     while len(lat) + failed < n:
         now = time.perf_counter() - t0
+        if now > limit_s:
+            break
+        if now - last_note > 10.0:
+            last_note = now
+            print(f"served: t={now:.0f}s submitted={i} done={len(lat)} failed={failed} "
+                  f"{imm.imm_server_info(srv)}", file=sys.stderr, flush=True)
         while i < n and qs[i].arrival_s <= now:
             q = qs[i]
             ids[imm.imm_server_submit(srv, q.graph_id, q.k, q.epsilon, q.ell, q.seed)] = i
@@ -544,6 +556,7 @@ def run_served(args, dist: Dist):
             "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
                            "max": float(lats.max()), "mean": float(lats.mean())},
             "offered_rate": args.served_rate, "completed": int(len(lat)), "failed": int(failed),
+            "submitted": int(i), "time_limited": bool(len(lat) + failed < n),
             "one_at_a_time": {"value": m / solo_s, "unit": "queries/s", "queries": m,
                               "results_identical_checked": len([j for j in keep if j < m])},
             "server": info, "roofline": None, "gpu_launches": None, "clocks": clk, "e2e": None,

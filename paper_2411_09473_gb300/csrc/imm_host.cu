@@ -41,6 +41,7 @@ struct Segment {
 
 constexpr double kE = 2.71828182845904523536;  // the double nearest e
 constexpr uint32_t kSelectCtaMaxN = 1u << 17;  // graphs this small select in one CTA
+constexpr size_t kServerIdlePerGraph = 8;       // workers a server keeps for reuse per graph
 
 }  // namespace
 
@@ -103,6 +104,7 @@ struct imm_ctx {
     uint64_t dev_bytes = 0;  // device bytes this context holds
     uint32_t next_batch = 1u << 22;
     double avg_len = 0.0;
+    double small_mean = 0.0;  // running mean members per small-path set
 
     // accounting for imm_stats
     double acc_sample_ms = 0, acc_select_ms = 0, acc_index_ms = 0;
@@ -258,6 +260,7 @@ void drop_stream(imm_ctx* c)
     c->list_members = 0;
     c->nbmp = 0;
     c->avg_len = 0.0;
+    c->small_mean = 0.0;
     c->next_batch = 1u << 22;
     if (c->off.p) cudaMemsetAsync(c->off.p, 0, sizeof(uint64_t), c->stream);
     if (c->cnt.p) cudaMemsetAsync(c->cnt.p, 0, (size_t)c->n * 4, c->stream);
@@ -474,11 +477,18 @@ int batch_phase1(imm_ctx* c, uint64_t theta)
         TRY(dalloc(c, c->scan_tmp, scan_tmp_words(cap) * 8));
         c->batch_cap = cap;
     }
-    // small-path staging: every small set holds at most small_cap members
-    const uint64_t stage_need = (uint64_t)count * small_cap(c->model);
-    if (c->stage_cap < stage_need) {
-        TRY(ensure(c, c->stage, stage_need * 4));
-        c->stage_cap = c->stage.bytes / 4;
+    // small-path staging: sized from the running mean small-set size (sets
+    // past it are resampled), never above count * small_cap, and always
+    // enough for one full small set
+    {
+        const double mean = c->small_mean > 0 ? c->small_mean * 1.5 + 8.0 : 64.0;
+        const uint64_t cap_all = (uint64_t)count * small_cap(c->model);
+        uint64_t need = std::min<uint64_t>(cap_all, (uint64_t)(mean * (double)count) + 4096);
+        need = std::max<uint64_t>(need, small_cap(c->model) + 4096);
+        if (c->stage_cap < need) {
+            TRY(ensure(c, c->stage, need * 4));
+            c->stage_cap = c->stage.bytes / 4;
+        }
     }
     // per-set arrays of the stream: room for base + count sets
     if (c->off_cap < c->nsets + count) {
@@ -649,6 +659,11 @@ int batch_phase3(imm_ctx* c, bool* progress)
     c->acc_edges += hs.edges;
     c->acc_sample_members += hs.all_members;
     c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : (1u << 22);
+    // running mean of the small-path set sizes of this batch
+    if (count > c->fb_large) {
+        const double m = (double)hs.stage_cursor / (double)(count - c->fb_large);
+        c->small_mean = c->small_mean > 0 ? std::max(m, 0.5 * (c->small_mean + m)) : m;
+    }
     if (c->segs.size() > 48) TRY(merge_segments(c));
     *progress = true;
     return IMM_OK;
@@ -1501,9 +1516,17 @@ void server_loop(imm_server* s)
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->active.empty() && s->pending.empty())
                 s->cv.wait_for(lk, std::chrono::milliseconds(2));
-            // admission: concurrency and device memory
-            while (!s->pending.empty() && s->active.size() < s->cfg.max_active &&
-                   (s->cfg.memory_budget_bytes == 0 || active_bytes(s) < s->cfg.memory_budget_bytes)) {
+            // admission: concurrency and device memory.  Idle workers are
+            // reclaimed when memory blocks admission, and one query is always
+            // admitted when none is in flight, so the queue always drains.
+            while (!s->pending.empty() && s->active.size() < s->cfg.max_active) {
+                if (s->cfg.memory_budget_bytes && active_bytes(s) >= s->cfg.memory_budget_bytes) {
+                    for (auto& v : s->idle) {
+                        for (imm_ctx* w : v) destroy_worker(w);
+                        v.clear();
+                    }
+                    if (!s->active.empty() && active_bytes(s) >= s->cfg.memory_budget_bytes) break;
+                }
                 ServedQuery* q = s->pending.front();
                 s->pending.pop_front();
                 q->admitted = std::chrono::steady_clock::now();
@@ -1530,10 +1553,20 @@ void server_loop(imm_server* s)
         ++s->waves;
         std::lock_guard<std::mutex> lk(s->mu);
         if (rc != IMM_OK) {
+            // the loop stops: every query in flight or still queued completes
+            // with the error, so no client waits forever
             s->fatal = rc;
             s->err = s->host->err;
             for (ServedQuery* q : s->active) {
                 if (q->job.stage < 4) job_fail(q->job, rc);
+            }
+            while (!s->pending.empty()) {
+                ServedQuery* q = s->pending.front();
+                s->pending.pop_front();
+                q->admitted = q->finished = std::chrono::steady_clock::now();
+                job_fail(q->job, rc);
+                s->done.push_back(q);
+                s->finished[q->id] = q;
             }
         }
         std::vector<ServedQuery*> still;
@@ -1543,7 +1576,10 @@ void server_loop(imm_server* s)
                 if (q->job.w) {
                     drop_stream(q->job.w);
                     cudaStreamSynchronize(q->job.w->stream);
-                    s->idle[q->graph].push_back(q->job.w);
+                    if (q->job.stage == 4 && s->idle[q->graph].size() < kServerIdlePerGraph)
+                        s->idle[q->graph].push_back(q->job.w);
+                    else
+                        destroy_worker(q->job.w);
                     q->job.w = nullptr;
                 }
                 s->done.push_back(q);

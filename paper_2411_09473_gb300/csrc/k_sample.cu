@@ -72,13 +72,13 @@ __device__ __forceinline__ uint32_t live_mask(uint4 w, uint4 th, uint32_t quad, 
     return live & 0xFu;
 }
 
-// Reserve space in the small-set staging (its capacity is exact, so failure
-// means a bookkeeping bug and is reported through the error word).
+// Reserve space in the small-set staging.  Its capacity is sized from the
+// running mean set size; a set that does not fit is marked failed and, with
+// every later set of the batch, resampled by the next batch.
 __device__ __forceinline__ bool reserve_small(const SampleBatch& b, uint32_t rel, uint32_t len, uint64_t* pos)
 {
     const unsigned long long p = atomicAdd(&b.sc->stage_cursor, (unsigned long long)len);
     if (p + len > b.stage_cap) {
-        atomicOr(&b.sc->error, kErrQueue);
         b.set_len[rel] = kLenFailed;
         atomicMin(&b.sc->first_fail, rel);
         return false;

@@ -71,3 +71,26 @@ def test_served_rejects_bad_queries(imm):
     with pytest.raises(imm.ImmError):
         imm.imm_server_take(srv, 12345, 5)                 # unknown id
     imm.imm_server_destroy(srv)
+
+
+def test_served_memory_bound_admission_still_drains(imm):
+    # a budget smaller than one query's working set: admission is memory-bound
+    # throughout, idle workers are reclaimed, and every query still completes
+    g = graphgen.make_graph(20000, 160000, 3, graphgen.IC, "inv_indeg")
+    ctx = load(imm, g)
+    srv = imm.imm_server_create([ctx], memory_budget_bytes=16 << 20, max_active=4)
+    qs = [(0, 10 + i, 0.3 + 0.01 * i, 1.0, 500 + i) for i in range(12)]
+    ids = {imm.imm_server_submit(srv, *q): q for q in qs}
+    got = {}
+    deadline = time.time() + 300
+    while len(got) < len(qs) and time.time() < deadline:
+        for (qid, status, _, _) in imm.imm_server_poll(srv):
+            got[qid] = (status, imm.imm_server_take(srv, qid, ids[qid][1]) if status == 0 else None)
+        time.sleep(0.005)
+    assert len(got) == len(qs)
+    imm.imm_server_destroy(srv)
+    for qid, (status, res) in got.items():
+        assert status == 0, status
+        gid, k, eps, ell, seed = ids[qid]
+        s2, _ = imm.imm_run(ctx, g.model, k, eps, ell, seed)
+        assert np.array_equal(res[0], s2)
