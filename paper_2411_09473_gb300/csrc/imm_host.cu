@@ -1008,6 +1008,48 @@ int job_after_select(Job& j, uint64_t cov)
 
 // One wave over the active jobs.  `master` is the stream of the selection
 // launch; `host` is the context that owns the device copy of the states.
+// Run fn(i) for i in [0, n) on up to `threads` host threads; the caller
+// makes sure that different i touch different contexts.
+template <class Fn>
+void parallel_for(size_t n, unsigned threads, Fn fn)
+{
+    if (n <= 2 || threads <= 1) {
+        for (size_t i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    const unsigned t = (unsigned)std::min<size_t>(threads, n);
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> pool;
+    for (unsigned i = 0; i < t; ++i) {
+        pool.emplace_back([&]() {
+            for (size_t q = next.fetch_add(1); q < n; q = next.fetch_add(1)) fn(q);
+        });
+    }
+    for (auto& th : pool) th.join();
+}
+
+unsigned wave_threads()
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    return std::max(1u, std::min(16u, hw ? hw : 1u));
+}
+
+// One sampling batch of one job: the three phases with its stream drained
+// in between (run concurrently across jobs by parallel_for).
+void job_sample_batch(Job* j)
+{
+    if (j->stage == 5) return;
+    imm_ctx* w = j->w;
+    int rc = batch_phase1(w, j->target);
+    if (rc == IMM_OK) rc = cudaStreamSynchronize(w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+    if (rc == IMM_OK) rc = batch_phase2(w);
+    if (rc == IMM_OK) rc = cudaStreamSynchronize(w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+    bool progress = false;
+    if (rc == IMM_OK) rc = batch_phase3(w, &progress);
+    if (rc != IMM_OK) job_fail(*j, rc);
+    else if (w->nsets >= j->target) ++j->stage;
+}
+
 int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64_t* launches)
 {
     std::vector<Job*> S;
@@ -1019,24 +1061,8 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         }
         S.push_back(j);
     }
-    for (Job* j : S) {
-        int rc = batch_phase1(j->w, j->target);
-        if (rc != IMM_OK) job_fail(*j, rc);
-    }
-    for (Job* j : S) {
-        if (j->stage == 5) continue;
-        int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
-        if (rc == IMM_OK) rc = batch_phase2(j->w);
-        if (rc != IMM_OK) job_fail(*j, rc);
-    }
-    for (Job* j : S) {
-        if (j->stage == 5) continue;
-        bool progress = false;
-        int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
-        if (rc == IMM_OK) rc = batch_phase3(j->w, &progress);
-        if (rc != IMM_OK) job_fail(*j, rc);
-        else if (j->w->nsets >= j->target) ++j->stage;
-    }
+    const unsigned threads = wave_threads();
+    parallel_for(S.size(), threads, [&](size_t i) { job_sample_batch(S[i]); });
     std::vector<Job*> L;
     for (Job* j : jobs)
         if (j->stage == 1 || j->stage == 3) L.push_back(j);
@@ -1046,15 +1072,20 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     std::vector<SelectState> states(L.size());
     std::vector<uint32_t> ks(L.size());
     std::vector<Job*> ok;
+    std::vector<SelectState> prep(L.size());
+    std::vector<int> prc(L.size(), IMM_OK);
+    parallel_for(L.size(), threads, [&](size_t t) {
+        prc[t] = select_prepare(L[t]->w, L[t]->k, &prep[t]);
+        if (prc[t] == IMM_OK) cudaEventRecord(L[t]->w->ev[4], L[t]->w->stream);
+    });
     for (size_t t = 0; t < L.size(); ++t) {
         Job* j = L[t];
-        int rc = select_prepare(j->w, j->k, &states[ok.size()]);
-        if (rc != IMM_OK) {
-            job_fail(*j, rc);
+        if (prc[t] != IMM_OK) {
+            job_fail(*j, prc[t]);
             continue;
         }
+        states[ok.size()] = prep[t];
         ks[ok.size()] = j->k;
-        cudaEventRecord(j->w->ev[4], j->w->stream);
         cudaStreamWaitEvent(master, j->w->ev[4], 0);
         ok.push_back(j);
     }

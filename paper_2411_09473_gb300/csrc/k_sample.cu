@@ -606,14 +606,24 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
     const bool smem_bm = ic_large_uses_smem(g.n, di) != 0;
     const uint32_t hcap = heavy_cap(g.n, smem_bm, di);
     const size_t smem = (smem_bm ? large_smem_bytes(g.n) : 0) + (size_t)(2 * hcap + 1) * 4;
+    // The opt-in limit is set to one fixed value (the device maximum less the
+    // kernel's static shared memory) whatever this launch needs, so host
+    // threads launching for graphs of different sizes never undercut each
+    // other's setting.
+    cudaFuncAttributes fa;
+    cudaError_t fe = smem_bm ? cudaFuncGetAttributes(&fa, ic_large_kernel<true>)
+                             : cudaFuncGetAttributes(&fa, ic_large_kernel<false>);
+    if (fe != cudaSuccess) return fe;
+    const int max_dyn = di.max_smem_optin - (int)fa.sharedSizeBytes;
+    if ((int)smem > max_dyn) return cudaErrorInvalidValue;
     if (smem_bm) {
-        cudaError_t e = cudaFuncSetAttribute(ic_large_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(ic_large_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
         if (e != cudaSuccess) return e;
         ic_large_kernel<true><<<grid, kLargeThreads, smem, st>>>(g, b, ls, hcap);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(ic_large_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(ic_large_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
         if (e != cudaSuccess) return e;
         ic_large_kernel<false><<<grid, kLargeThreads, smem, st>>>(g, b, ls, hcap);
     }
