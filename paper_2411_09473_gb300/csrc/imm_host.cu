@@ -16,6 +16,7 @@
 #include <unordered_map>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1028,10 +1029,28 @@ void parallel_for(size_t n, unsigned threads, Fn fn)
     for (auto& th : pool) th.join();
 }
 
+// Host threads per wave (environment IMM_WAVE_THREADS, default 1): a tuning
+// knob only; results never depend on it.
 unsigned wave_threads()
 {
-    const unsigned hw = std::thread::hardware_concurrency();
-    return std::max(1u, std::min(16u, hw ? hw : 1u));
+    static const unsigned t = []() {
+        const char* e = std::getenv("IMM_WAVE_THREADS");
+        const int v = e ? std::atoi(e) : 1;
+        return (unsigned)std::max(1, std::min(64, v));
+    }();
+    return t;
+}
+
+// Per-wave trace lines on stderr when the environment sets IMM_TRACE.
+bool trace_on()
+{
+    static const bool on = std::getenv("IMM_TRACE") != nullptr;
+    return on;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
 }
 
 // One sampling batch of one job: the three phases with its stream drained
@@ -1062,11 +1081,17 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         S.push_back(j);
     }
     const unsigned threads = wave_threads();
+    const auto tw0 = std::chrono::steady_clock::now();
     parallel_for(S.size(), threads, [&](size_t i) { job_sample_batch(S[i]); });
+    const double t_sample = ms_since(tw0);
     std::vector<Job*> L;
     for (Job* j : jobs)
         if (j->stage == 1 || j->stage == 3) L.push_back(j);
-    if (L.empty()) return IMM_OK;
+    if (L.empty()) {
+        if (trace_on()) fprintf(stderr, "imm wave: sample %zu jobs %.2f ms\n", S.size(), t_sample);
+        return IMM_OK;
+    }
+    const auto tp0 = std::chrono::steady_clock::now();
     // selection: prepare each job's state on its stream, one launch for all
     const size_t rec = sizeof(SelectState);
     std::vector<SelectState> states(L.size());
@@ -1111,7 +1136,18 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         j->w->acc_launches += 1;
         if (select_readback(j->w, j->k, master) != IMM_OK) e = cudaErrorUnknown;
     }
+    const double t_prep = ms_since(tp0);
+    const auto ts0 = std::chrono::steady_clock::now();
     if (e == cudaSuccess) e = cudaStreamSynchronize(master);
+    if (trace_on()) {
+        uint32_t kmax = 0, nmax = 0;
+        for (Job* j : ok) {
+            kmax = std::max(kmax, j->k);
+            nmax = std::max(nmax, j->w->n);
+        }
+        fprintf(stderr, "imm wave: sample %zu jobs %.2f ms | select %zu jobs: prepare %.2f ms, kernel+sync %.2f ms "
+                        "(k<=%u, n<=%u)\n", S.size(), t_sample, ok.size(), t_prep, ms_since(ts0), kmax, nmax);
+    }
     cudaFreeHost(hbuf);
     if (e != cudaSuccess) return cuda_err(host, e, "batched selection");
     for (Job* j : ok) {
