@@ -1009,38 +1009,6 @@ int job_after_select(Job& j, uint64_t cov)
 
 // One wave over the active jobs.  `master` is the stream of the selection
 // launch; `host` is the context that owns the device copy of the states.
-// Run fn(i) for i in [0, n) on up to `threads` host threads; the caller
-// makes sure that different i touch different contexts.
-template <class Fn>
-void parallel_for(size_t n, unsigned threads, Fn fn)
-{
-    if (n <= 2 || threads <= 1) {
-        for (size_t i = 0; i < n; ++i) fn(i);
-        return;
-    }
-    const unsigned t = (unsigned)std::min<size_t>(threads, n);
-    std::atomic<size_t> next{0};
-    std::vector<std::thread> pool;
-    for (unsigned i = 0; i < t; ++i) {
-        pool.emplace_back([&]() {
-            for (size_t q = next.fetch_add(1); q < n; q = next.fetch_add(1)) fn(q);
-        });
-    }
-    for (auto& th : pool) th.join();
-}
-
-// Host threads per wave (environment IMM_WAVE_THREADS, default 1): a tuning
-// knob only; results never depend on it.
-unsigned wave_threads()
-{
-    static const unsigned t = []() {
-        const char* e = std::getenv("IMM_WAVE_THREADS");
-        const int v = e ? std::atoi(e) : 1;
-        return (unsigned)std::max(1, std::min(64, v));
-    }();
-    return t;
-}
-
 // Per-wave trace lines on stderr when the environment sets IMM_TRACE.
 bool trace_on()
 {
@@ -1051,22 +1019,6 @@ bool trace_on()
 double ms_since(std::chrono::steady_clock::time_point t)
 {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
-}
-
-// One sampling batch of one job: the three phases with its stream drained
-// in between (run concurrently across jobs by parallel_for).
-void job_sample_batch(Job* j)
-{
-    if (j->stage == 5) return;
-    imm_ctx* w = j->w;
-    int rc = batch_phase1(w, j->target);
-    if (rc == IMM_OK) rc = cudaStreamSynchronize(w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
-    if (rc == IMM_OK) rc = batch_phase2(w);
-    if (rc == IMM_OK) rc = cudaStreamSynchronize(w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
-    bool progress = false;
-    if (rc == IMM_OK) rc = batch_phase3(w, &progress);
-    if (rc != IMM_OK) job_fail(*j, rc);
-    else if (w->nsets >= j->target) ++j->stage;
 }
 
 int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64_t* launches)
@@ -1080,9 +1032,27 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         }
         S.push_back(j);
     }
-    const unsigned threads = wave_threads();
+    // phase-major: every job's launches are issued before any stream is
+    // drained, so the jobs' kernels overlap on the GPU
     const auto tw0 = std::chrono::steady_clock::now();
-    parallel_for(S.size(), threads, [&](size_t i) { job_sample_batch(S[i]); });
+    for (Job* j : S) {
+        const int rc = batch_phase1(j->w, j->target);
+        if (rc != IMM_OK) job_fail(*j, rc);
+    }
+    for (Job* j : S) {
+        if (j->stage == 5) continue;
+        int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+        if (rc == IMM_OK) rc = batch_phase2(j->w);
+        if (rc != IMM_OK) job_fail(*j, rc);
+    }
+    for (Job* j : S) {
+        if (j->stage == 5) continue;
+        bool progress = false;
+        int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+        if (rc == IMM_OK) rc = batch_phase3(j->w, &progress);
+        if (rc != IMM_OK) job_fail(*j, rc);
+        else if (j->w->nsets >= j->target) ++j->stage;
+    }
     const double t_sample = ms_since(tw0);
     std::vector<Job*> L;
     for (Job* j : jobs)
@@ -1099,10 +1069,10 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     std::vector<Job*> ok;
     std::vector<SelectState> prep(L.size());
     std::vector<int> prc(L.size(), IMM_OK);
-    parallel_for(L.size(), threads, [&](size_t t) {
+    for (size_t t = 0; t < L.size(); ++t) {
         prc[t] = select_prepare(L[t]->w, L[t]->k, &prep[t]);
         if (prc[t] == IMM_OK) cudaEventRecord(L[t]->w->ev[4], L[t]->w->stream);
-    });
+    }
     for (size_t t = 0; t < L.size(); ++t) {
         Job* j = L[t];
         if (prc[t] != IMM_OK) {
