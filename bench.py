@@ -36,7 +36,15 @@ METRIC = "IMM seconds-to-seeds"
 # the current kernel on the first 2,000 sets of the 1M-vertex IC workload
 # (profiles/ic_large_kernel__ic_u01_1m_first2000sets.md: 12.454 GB over
 # 4,620,412,076 in-edges).  Traffic of a full launch is scaled by its in-edges.
-IC_LARGE_DRAM_BYTES_PER_EDGE = 12.454e9 / 4620412076
+# IC sampling is bound by integer issue, not by DRAM: its roofline counts coin
+# evaluations, one per (RRR set, in-edge quad) pair the BFS examines, each a
+# Philox4x32-10 draw (10 rounds of 2 wide 32x32 multiplies + 2 three-input
+# xors = 40 instructions) and 4 threshold compares, against the issue rate of
+# the GPU (SMs x 4 schedulers x 32 lanes x max SM clock).
+ALU_OPS_PER_QUAD_EVAL = 44
+# DRAM bytes per quad evaluation of the dominant IC kernel, from one ncu capture
+# (profiles/ic_group_kernel__ic_u01_1m_first2000sets.md); None until captured.
+IC_DRAM_BYTES_PER_QUAD_EVAL = 3.565422e9 / 1192743275
 WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "batch64", "served")
 
 
@@ -313,10 +321,37 @@ def run_gpu(args, dist: Dist):
     edges = sum(s.sample_edges for s in stats)
     members = sum(s.sample_members for s in stats)
     launches = sum(s.sample_launches for s in stats)
-    algo_bytes = 8.0 * edges + 16.0 * members
-    achieved = algo_bytes / (ms_sample / 1e3) / 1e9 if ms_sample > 0 else 0.0
-    peak, peak_kind = measured_peaks()
     st = stats[-1]
+    if g.model == graphgen.IC:
+        # every step samples the same stream: count its quad evaluations once
+        cnt = imm.imm_get_counts(ctx, g.n).astype(np.float64)
+        row = g.row.astype(np.int64)
+        deg = np.diff(row)
+        quads = np.where(deg > 0, ((row[1:] - 1) >> 2) - (row[:-1] >> 2) + 1, 0).astype(np.float64)
+        evals = float((cnt * quads).sum()) * len(stats)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_max_mhz") or 2070.0
+        peak = sms * 4 * 32 * mhz * 1e6 / 1e12
+        achieved = ALU_OPS_PER_QUAD_EVAL * evals / (ms_sample / 1e3) / 1e12 if ms_sample > 0 else 0.0
+        roof = {"kernel": "RRR sampling (IC): ic_group_kernel / ic_large_kernel + ic_small_kernel",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "peak_kind": f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz",
+                "traffic": (IC_DRAM_BYTES_PER_QUAD_EVAL * evals / max(launches, 1)
+                            if IC_DRAM_BYTES_PER_QUAD_EVAL else None),
+                "traffic_source": "ncu dram__bytes_read+write per quad evaluation of the dominant kernel, "
+                                  "scaled to the average timed launch",
+                "algorithmic_ops": f"{ALU_OPS_PER_QUAD_EVAL} integer instructions per (set, in-edge quad) "
+                                   "coin evaluation",
+                "quad_evals_per_launch": evals / max(launches, 1), "launches": launches}
+    else:
+        algo_bytes = 8.0 * edges + 16.0 * members
+        achieved = algo_bytes / (ms_sample / 1e3) / 1e9 if ms_sample > 0 else 0.0
+        peak, peak_kind = measured_peaks()
+        roof = {"kernel": "RRR sampling (LT): lt_small_kernel + lt_long_kernel", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes": "8 B per walk step + 16 B per member",
+                "algorithmic_bytes_per_launch": algo_bytes / max(launches, 1), "launches": launches}
     gteps = (st.sample_edges / (st.ms_sample / 1e3)) / 1e9 if st.ms_sample > 0 else 0.0
 
     e2e = None
@@ -370,16 +405,7 @@ def run_gpu(args, dist: Dist):
             "imm": {"theta": st.theta, "num_sets": st.num_sets, "members": st.members, "rounds": st.rounds,
                     "lb": st.lb, "covered": st.covered, "ms_sample": st.ms_sample, "ms_index": st.ms_index,
                     "ms_select": st.ms_select, "seeds_head": [int(x) for x in seeds[:10]]},
-            "roofline": {"kernel": "RRR sampling: ic_large_kernel (98.8% of device time) + ic_small_kernel",
-                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": (IC_LARGE_DRAM_BYTES_PER_EDGE * edges / max(launches, 1)
-                                     if args.workload == "ic_u01_1m" else None),
-                         "traffic_source": ("ncu dram__bytes_read+write per in-edge of ic_large_kernel, scaled "
-                                            "to the average timed launch" if args.workload == "ic_u01_1m" else None),
-                         "algorithmic_bytes": "8 B per examined in-edge + 16 B per member",
-                         "algorithmic_bytes_per_launch": algo_bytes / max(launches, 1),
-                         "launches": launches},
+            "roofline": roof,
             "gpu_launches": int(sum(s.kernel_launches for s in stats)),
             "clocks": clk,
             "e2e": e2e,

@@ -93,6 +93,7 @@ struct imm_ctx {
     DBuf scalars;
     DBuf scan_tmp;
     DBuf slot_q, slot_bm;
+    DBuf grp;  // grouped IC large path: masks, frontier lists, large-vertex list, counters
     uint32_t nslots = 0;
     uint64_t slot_words = 0;
     DBuf hist, cursor, vtmp;
@@ -106,6 +107,7 @@ struct imm_ctx {
     uint32_t next_batch = 1u << 22;
     double avg_len = 0.0;
     double small_mean = 0.0;  // running mean members per small-path set
+    double large_mean = 0.0;  // running mean members per large-path set
 
     // accounting for imm_stats
     double acc_sample_ms = 0, acc_select_ms = 0, acc_index_ms = 0;
@@ -262,6 +264,7 @@ void drop_stream(imm_ctx* c)
     c->nbmp = 0;
     c->avg_len = 0.0;
     c->small_mean = 0.0;
+    c->large_mean = 0.0;
     c->next_batch = 1u << 22;
     if (c->off.p) cudaMemsetAsync(c->off.p, 0, sizeof(uint64_t), c->stream);
     if (c->cnt.p) cudaMemsetAsync(c->cnt.p, 0, (size_t)c->n * 4, c->stream);
@@ -288,6 +291,7 @@ void free_graph(imm_ctx* c)
     dfree(c, c->picked);
     dfree(c, c->slot_q);
     dfree(c, c->slot_bm);
+    dfree(c, c->grp);
     c->nslots = 0;
     c->loaded = false;
 }
@@ -392,6 +396,52 @@ int ensure_slots(imm_ctx* c, uint32_t want_slots, bool need_bitmap)
     c->nslots = want_slots;
     c->slot_words = words;
     return IMM_OK;
+}
+
+// Scratch of the grouped IC large path (carved from one buffer; the masks
+// start at zero and every launch leaves them zero).
+int ensure_group(imm_ctx* c, GroupScratch* gs)
+{
+    const uint64_t n = c->n;
+    const uint64_t hcap = ic_group_heavy_cap(c->n, c->m);
+    auto up = [](uint64_t x) { return (x + 255) & ~255ull; };
+    const uint64_t o_fr0 = up(n * 8), o_fr1 = o_fr0 + up(n * 8), o_lq0 = o_fr1 + up(n * 8);
+    const uint64_t o_lq1 = o_lq0 + up(n * 4), o_hb0 = o_lq1 + up(n * 4), o_hb1 = o_hb0 + up(hcap * 4);
+    const uint64_t o_he0 = o_hb1 + up(hcap * 4), o_he1 = o_he0 + up(hcap * 16), o_ct = o_he1 + up(hcap * 16);
+    const uint64_t bytes = o_ct + up(sizeof(GroupCounters));
+    if (c->grp.bytes < bytes) {
+        TRY(dalloc(c, c->grp, bytes));
+        CK(cudaMemsetAsync(c->grp.p, 0, o_lq0, c->stream));
+    }
+    char* p = static_cast<char*>(c->grp.p);
+    gs->vis = reinterpret_cast<unsigned long long*>(p);
+    gs->fr0 = reinterpret_cast<unsigned long long*>(p + o_fr0);
+    gs->fr1 = reinterpret_cast<unsigned long long*>(p + o_fr1);
+    gs->lq0 = reinterpret_cast<uint32_t*>(p + o_lq0);
+    gs->lq1 = reinterpret_cast<uint32_t*>(p + o_lq1);
+    gs->hb0 = reinterpret_cast<uint32_t*>(p + o_hb0);
+    gs->hb1 = reinterpret_cast<uint32_t*>(p + o_hb1);
+    gs->he0 = reinterpret_cast<uint4*>(p + o_he0);
+    gs->he1 = reinterpret_cast<uint4*>(p + o_he1);
+    gs->ctr = reinterpret_cast<GroupCounters*>(p + o_ct);
+    return IMM_OK;
+}
+
+// The grouped path pays two dense passes over n per group of 64 sets and a
+// grid barrier per BFS level, so it is taken when there are enough large sets and
+// they are big (judged from the previous batches); it launches cooperatively,
+// so contexts whose streams run beside others' (batch and server workers)
+// keep the one-set-per-CTA path.
+// IMM_IC_LARGE=cta|group overrides the choice (both give the same sets).
+bool use_group(const imm_ctx* c, uint32_t large_count)
+{
+    if (c->model != IMM_IC || c->borrowed || large_count == 0) return false;
+    const char* force = getenv("IMM_IC_LARGE");
+    if (force && strcmp(force, "cta") == 0) return false;
+    if (!ic_group_supported(c->di)) return false;
+    if (force && strcmp(force, "group") == 0) return true;
+    if (large_count < kGroupSets) return false;
+    return c->large_mean <= 0.0 || c->large_mean * kGroupSets >= (double)c->n / 4.0;
 }
 
 int index_limit_ok(imm_ctx* c, uint64_t more_bytes)
@@ -504,6 +554,7 @@ int batch_phase1(imm_ctx* c, uint64_t theta)
     CK(cudaMemsetAsync(&sc->first_fail, 0xFF, 4, c->stream));
     SampleBatch& b = c->fb;
     b.seed = c->seed;
+    b.rk = philox_keys(c->seed);
     b.base = c->nsets;
     b.count = count;
     b.words = words;
@@ -549,25 +600,33 @@ int batch_phase2(imm_ctx* c)
         b.big = P<uint32_t>(c->big);
         b.big_cap = c->big_cap;
         const bool ic = c->model == IMM_IC;
-        const uint32_t want_slots =
-            std::min<uint32_t>(large_count, ic ? (uint32_t)c->di.sms : (uint32_t)std::min(c->di.sms * 2, 1024));
-        if (ic) {
-            const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
-            TRY(ensure_slots(c, want_slots, !smem));
-        } else {
-            TRY(ensure_slots(c, want_slots, true));
-        }
-        LargeSlots ls;
-        ls.queues = P<uint32_t>(c->slot_q);
-        ls.queue_cap = c->n;
-        ls.bitmaps = P<uint32_t>(c->slot_bm);
-        ls.bitmap_words = words;
-        ls.nslots = std::min<uint32_t>(c->nslots, large_count);
         const DevGraph g = dev_graph(c);
-        CK(cudaEventRecord(c->ev[2], c->stream));
-        if (ic) CK(launch_ic_large(g, b, ls, c->di, c->stream));
-        else CK(launch_lt_long(g, b, ls, c->di, c->stream));
-        CK(cudaEventRecord(c->ev[3], c->stream));
+        if (use_group(c, large_count)) {
+            GroupScratch gs;
+            TRY(ensure_group(c, &gs));
+            CK(cudaEventRecord(c->ev[2], c->stream));
+            CK(launch_ic_group(g, b, gs, c->di, c->stream));
+            CK(cudaEventRecord(c->ev[3], c->stream));
+        } else {
+            const uint32_t want_slots = std::min<uint32_t>(
+                large_count, ic ? (uint32_t)c->di.sms : (uint32_t)std::min(c->di.sms * 2, 1024));
+            if (ic) {
+                const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
+                TRY(ensure_slots(c, want_slots, !smem));
+            } else {
+                TRY(ensure_slots(c, want_slots, true));
+            }
+            LargeSlots ls;
+            ls.queues = P<uint32_t>(c->slot_q);
+            ls.queue_cap = c->n;
+            ls.bitmaps = P<uint32_t>(c->slot_bm);
+            ls.bitmap_words = words;
+            ls.nslots = std::min<uint32_t>(c->nslots, large_count);
+            CK(cudaEventRecord(c->ev[2], c->stream));
+            if (ic) CK(launch_ic_large(g, b, ls, c->di, c->stream));
+            else CK(launch_lt_long(g, b, ls, c->di, c->stream));
+            CK(cudaEventRecord(c->ev[3], c->stream));
+        }
         c->acc_sample_launches += 1;
         c->acc_launches += 1;
     }
@@ -664,6 +723,10 @@ int batch_phase3(imm_ctx* c, bool* progress)
     if (count > c->fb_large) {
         const double m = (double)hs.stage_cursor / (double)(count - c->fb_large);
         c->small_mean = c->small_mean > 0 ? std::max(m, 0.5 * (c->small_mean + m)) : m;
+    }
+    if (c->fb_large && hs.all_members > hs.stage_cursor) {
+        const double m = (double)(hs.all_members - hs.stage_cursor) / (double)c->fb_large;
+        c->large_mean = c->large_mean > 0 ? 0.5 * (c->large_mean + m) : m;
     }
     if (c->segs.size() > 48) TRY(merge_segments(c));
     *progress = true;
@@ -1160,6 +1223,7 @@ int imm_create(imm_ctx** out, int device, const imm_alloc* alloc, void* stream)
     }
     c->di.sms = prop.multiProcessorCount;
     c->di.max_smem_optin = (int)prop.sharedMemPerBlockOptin;
+    c->di.cooperative = prop.cooperativeLaunch;
     for (auto& e : c->ev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
             delete c;

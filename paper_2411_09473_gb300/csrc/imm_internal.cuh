@@ -25,31 +25,94 @@ constexpr int kErrBadGraph = 4;
 // -> 64-bit products whose halves are xored with the other counter words and
 // the round key; the key advances by the Weyl constants between rounds.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+// The ten round keys of one 64-bit key: k[2r], k[2r+1] are round r's words.
+// Kernels receive them as parameters, so every round's xor reads its key
+// straight from the constant bank instead of advancing it in registers.
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys rk;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0;
+        rk.k[2 * r + 1] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return rk;
+}
+
+__host__ __device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
+{
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)c.x;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)c.z;
+    return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
+
+__host__ __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys& rk)
 {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
-        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
-    }
+    for (int r = 0; r < 10; ++r) c = philox_round(c, rk.k[2 * r], rk.k[2 * r + 1]);
     return c;
 }
 
-__device__ __forceinline__ uint2 philox_key(uint64_t seed)
+// All draws of one RRR set use counters (s_lo, s_hi, x, tag) that differ in
+// word 2 only.  Round 0 multiplies words 0 and 2, so its half fed by word 0
+// (and word 3) is the same for every x; round 1 then multiplies that half's
+// output again.  PhiloxSet holds those x-independent values, pre-xored with
+// the round keys they meet, so a draw costs 1 + 1 + 2 x 8 products instead of
+// 2 x 10 (the result is bit-identical to philox()).
+struct PhiloxSet {
+    uint32_t r0;    // round 0, word 0: s_hi ^ k0(0)
+    uint32_t r1a;   // round 1, word 0: hi(M1 * a2) ^ k0(1)
+    uint32_t r1b;   // round 1, word 2: a3 ^ k1(1)
+    uint32_t r2;    // round 2, word 0: lo(M1 * a2) ^ k0(2)
+};
+
+__host__ __device__ __forceinline__ PhiloxSet philox_set(uint32_t s_lo, uint32_t s_hi, uint32_t tag,
+                                                        const PhiloxKeys& rk)
 {
-    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)s_lo;
+    const uint32_t a2 = (uint32_t)(p0 >> 32) ^ tag ^ rk.k[1];  // round 0, word 2
+    const uint32_t a3 = (uint32_t)p0;                          // round 0, word 3
+    const uint64_t b = (uint64_t)kPhiloxM1 * (uint64_t)a2;       // round 1, product of word 2
+    PhiloxSet ps;
+    ps.r0 = s_hi ^ rk.k[0];
+    ps.r1a = (uint32_t)(b >> 32) ^ rk.k[2];
+    ps.r1b = a3 ^ rk.k[3];
+    ps.r2 = (uint32_t)b ^ rk.k[4];
+    return ps;
+}
+
+// philox((s_lo, s_hi, x, tag), key) for the set `ps` was built from.
+__host__ __device__ __forceinline__ uint4 philox_x(uint32_t x, const PhiloxSet& ps, const PhiloxKeys& rk)
+{
+    // round 0: only the product of word 2 (= x) depends on x
+    const uint64_t a = (uint64_t)kPhiloxM1 * (uint64_t)x;
+    const uint32_t x0 = (uint32_t)(a >> 32) ^ ps.r0, x1 = (uint32_t)a;
+    // round 1: counter (x0, x1, a2, a3); the product of a2 is in ps
+    const uint64_t p = (uint64_t)kPhiloxM0 * (uint64_t)x0;
+    // round 2: counter (y0, lo(M1 a2), y2, y3)
+    const uint32_t y0 = x1 ^ ps.r1a, y2 = (uint32_t)(p >> 32) ^ ps.r1b, y3 = (uint32_t)p;
+    const uint64_t q0 = (uint64_t)kPhiloxM0 * (uint64_t)y0;
+    const uint64_t q1 = (uint64_t)kPhiloxM1 * (uint64_t)y2;
+    uint4 c = make_uint4((uint32_t)(q1 >> 32) ^ ps.r2, (uint32_t)q1, (uint32_t)(q0 >> 32) ^ y3 ^ rk.k[5],
+                         (uint32_t)q0);
+#pragma unroll
+    for (int r = 3; r < 10; ++r) c = philox_round(c, rk.k[2 * r], rk.k[2 * r + 1]);
+    return c;
 }
 
 // Root of set s: uniform over [0, n) by multiply-shift of a 64-bit draw.
-__device__ __forceinline__ uint32_t draw_root(uint64_t seed, uint64_t s, uint32_t n)
+__device__ __forceinline__ uint32_t draw_root(const PhiloxKeys& rk, uint64_t s, uint32_t n)
 {
-    const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), 0u, kTagRoot), philox_key(seed));
+    const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), 0u, kTagRoot), rk);
     const uint64_t x = ((uint64_t)w.y << 32) | w.x;
     return (uint32_t)__umul64hi(x, (uint64_t)n);
 }
@@ -89,6 +152,7 @@ constexpr uint64_t kBigFlag = 1ull << 63;  // set_pos points into the large-outp
 
 struct SampleBatch {
     uint64_t seed;
+    PhiloxKeys rk;        // round keys of `seed`
     uint64_t base;        // first set id of the batch
     uint32_t count;       // sets in the batch
     uint32_t words;       // ceil(n / 32): words of one n-bit bitmap
@@ -103,6 +167,26 @@ struct SampleBatch {
     uint32_t* large_q;    // [count] batch-relative ids for the large-set path
     BatchScalars* sc;
 };
+
+// Reserve space for a large set's output (list of len members, or a bitmap
+// of b.words words).  When the buffer is full the set is marked failed; it
+// and every later set of the batch are resampled by the next batch.
+__device__ __forceinline__ bool reserve_big(const SampleBatch& b, uint32_t rel, uint32_t len, uint32_t kind,
+                                            uint64_t* pos)
+{
+    const uint64_t size = kind ? (uint64_t)b.words : (uint64_t)len;
+    const unsigned long long p = atomicAdd(&b.sc->big_cursor, (unsigned long long)size);
+    if (p + size > b.big_cap) {
+        b.set_len[rel] = kLenFailed;
+        atomicMin(&b.sc->first_fail, rel);
+        return false;
+    }
+    *pos = p;
+    b.set_pos[rel] = p | kBigFlag;
+    b.set_len[rel] = len;
+    b.set_kind[rel] = kind;
+    return true;
+}
 
 // Per-CTA scratch of the large-set path: a member queue of n entries and,
 // when the visited bitmap does not fit in shared memory, an n-bit bitmap.
@@ -139,6 +223,7 @@ struct BatchOut {
 struct DeviceInfo {
     int sms;
     int max_smem_optin;
+    int cooperative;  // cooperative launches supported
 };
 
 // graph
@@ -157,6 +242,35 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
 cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
                            const DeviceInfo& di, cudaStream_t st);
+// Grouped IC large path: the large sets of a batch, 64 at a time, as one
+// multi-source BFS over the whole GPU (cooperative launch).
+constexpr uint32_t kGroupSets = 64;
+struct GroupCounters {
+    unsigned long long hpack[3];      // large frontier vertices << 40 | their chunks, by level mod 3
+    uint32_t lcount[3];               // small frontier vertices, by level mod 3
+    uint32_t claim[3];                // work items claimed, by level mod 3
+    uint32_t cnt[kGroupSets];         // members per set
+    uint32_t edges[kGroupSets];       // in-edges of the members per set
+    uint32_t kind[kGroupSets];        // 0 list, 1 bitmap, 2 reservation failed
+    unsigned long long pos[kGroupSets];   // output position in the large-output buffer
+    unsigned long long lcur[kGroupSets];  // list entries written
+};
+struct GroupScratch {
+    unsigned long long* vis;  // [n] sets of the group that expanded v (zero between groups)
+    unsigned long long* fr0;  // [n] frontier masks, even levels (zero outside the frontier)
+    unsigned long long* fr1;  // [n] odd levels
+    uint32_t* lq0;            // [n] small frontier vertices, even levels
+    uint32_t* lq1;            // [n] odd levels
+    uint32_t* hb0;            // [hcap] first chunk of each large frontier vertex, even levels
+    uint32_t* hb1;            // [hcap] odd levels
+    uint4* he0;               // [hcap] (v, rs, re, chunks left), even levels
+    uint4* he1;               // [hcap] odd levels
+    GroupCounters* ctr;
+};
+int ic_group_supported(const DeviceInfo& di);
+uint64_t ic_group_heavy_cap(uint32_t n, uint64_t m);
+cudaError_t launch_ic_group(const DevGraph& g, const SampleBatch& b, const GroupScratch& gs, const DeviceInfo& di,
+                            cudaStream_t st);
 // Scan of the kept sets: list offsets into off[], bitmap ranks, totals.
 uint64_t scan_tmp_words(uint32_t count);
 cudaError_t launch_batch_scan(const SampleBatch& b, const BatchOut& o, uint64_t* tmp, const DeviceInfo& di,

@@ -90,26 +90,6 @@ __device__ __forceinline__ bool reserve_small(const SampleBatch& b, uint32_t rel
     return true;
 }
 
-// Reserve space for a large set's output (list of len members, or a bitmap
-// of b.words words).  When the buffer is full the set is marked failed; it
-// and every later set of the batch are resampled by the next batch.
-__device__ __forceinline__ bool reserve_big(const SampleBatch& b, uint32_t rel, uint32_t len, uint32_t kind,
-                                            uint64_t* pos)
-{
-    const uint64_t size = kind ? (uint64_t)b.words : (uint64_t)len;
-    const unsigned long long p = atomicAdd(&b.sc->big_cursor, (unsigned long long)size);
-    if (p + size > b.big_cap) {
-        b.set_len[rel] = kLenFailed;
-        atomicMin(&b.sc->first_fail, rel);
-        return false;
-    }
-    *pos = p;
-    b.set_pos[rel] = p | kBigFlag;
-    b.set_len[rel] = len;
-    b.set_kind[rel] = kind;
-    return true;
-}
-
 // ===========================================================================
 // IC, small path: one warp per set.
 // ===========================================================================
@@ -142,7 +122,6 @@ ic_small_kernel(DevGraph g, SampleBatch b)
     uint16_t* lslot = sh_slot[wid];
     uint32_t* hash = sh_hash[wid];
     const uint32_t ltm = lanemask_lt();
-    const uint2 key = philox_key(b.seed);
 
     for (uint32_t i = lane; i < kSmallHash; i += 32) hash[i] = kEmpty;
     __syncwarp();
@@ -153,9 +132,9 @@ ic_small_kernel(DevGraph g, SampleBatch b)
         rel = __shfl_sync(kFull, rel, 0);
         if (rel >= b.count) break;
         const uint64_t s = b.base + rel;
-        const uint32_t s_lo = (uint32_t)s, s_hi = (uint32_t)(s >> 32);
+        const PhiloxSet ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagIC, b.rk);
         if (lane == 0) {
-            const uint32_t root = draw_root(b.seed, s, g.n);
+            const uint32_t root = draw_root(b.rk, s, g.n);
             const uint32_t sl = small_slot(root);
             hash[sl] = root;
             list[0] = root;
@@ -201,7 +180,7 @@ ic_small_kernel(DevGraph g, SampleBatch b)
                 if (j < total) {
                     quad = (ors >> 2) + (j - oex);
                     const uint4 th = load_thr4(g.thr, quad);
-                    const uint4 w = philox(make_uint4(s_lo, s_hi, quad, kTagIC), key);
+                    const uint4 w = philox_x(quad, ps, b.rk);
                     live = live_mask(w, th, quad, ors, ore);
                 }
 #pragma unroll
@@ -308,15 +287,15 @@ __device__ __forceinline__ void visit_live(uint32_t live, uint32_t quad, const u
 
 constexpr uint32_t kWarpBuf = 128;
 __device__ __forceinline__ void expand_pair(uint32_t qa, bool ha, uint32_t rsa, uint32_t rea, uint32_t qb, bool hb,
-                                            uint32_t rsb, uint32_t reb, uint32_t s_lo, uint32_t s_hi, uint2 key,
+                                            uint32_t rsb, uint32_t reb, const PhiloxSet& ps, const PhiloxKeys& rk,
                                             const DevGraph& g, uint32_t* bm, uint32_t* q, uint32_t* s_tail,
                                             uint32_t* wbuf)
 {
     uint4 tha = make_uint4(0, 0, 0, 0), thb = tha, wa = tha, wb = tha;
     if (ha) tha = load_thr4(g.thr, qa);
     if (hb) thb = load_thr4(g.thr, qb);
-    if (ha) wa = philox(make_uint4(s_lo, s_hi, qa, kTagIC), key);
-    if (hb) wb = philox(make_uint4(s_lo, s_hi, qb, kTagIC), key);
+    if (ha) wa = philox_x(qa, ps, rk);
+    if (hb) wb = philox_x(qb, ps, rk);
     uint32_t la = ha ? live_mask(wa, tha, qa, rsa, rea) : 0u;
     uint32_t lb = hb ? live_mask(wb, thb, qb, rsb, reb) : 0u;
     const int lane = threadIdx.x & 31;
@@ -376,7 +355,6 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
     uint32_t* s_hv = dyn + bm_words;
     uint32_t* s_hpre = s_hv + hcap;
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
-    const uint2 key = philox_key(b.seed);
     const uint32_t large_count = b.sc->large_count;  // final: written by the previous launch
 
     if (kSmemBitmap)
@@ -392,9 +370,9 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
         if (idx >= large_count) break;
         const uint32_t rel = b.large_q[idx];
         const uint64_t s = b.base + rel;
-        const uint32_t s_lo = (uint32_t)s, s_hi = (uint32_t)(s >> 32);
+        const PhiloxSet ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagIC, b.rk);
         if (tid == 0) {
-            const uint32_t root = draw_root(b.seed, s, g.n);
+            const uint32_t root = draw_root(b.rk, s, g.n);
             q[0] = root;
             bm[root >> 5] |= 1u << (root & 31);
             s_tail = 1;
@@ -440,7 +418,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     const uint32_t q1 = (ore - 1) >> 2;
                     for (uint32_t q0 = (ors >> 2); q0 <= q1; q0 += 64) {
                         const uint32_t qa = q0 + lane;
-                        expand_pair(qa, qa <= q1, ors, ore, qa + 32, qa + 32 <= q1, ors, ore, s_lo, s_hi, key, g, bm,
+                        expand_pair(qa, qa <= q1, ors, ore, qa + 32, qa + 32 <= q1, ors, ore, ps, b.rk, g, bm,
                                     q, &s_tail, wbuf);
                     }
                 }
@@ -470,7 +448,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     const bool ha = ja < total, hb = jb < total;
                     const uint32_t qa = (rsa >> 2) + (ja - exa);
                     const uint32_t qb = (rsb >> 2) + (jb - exb);
-                    expand_pair(qa, ha, rsa, rea, qb, hb, rsb, reb, s_lo, s_hi, key, g, bm, q, &s_tail, wbuf);
+                    expand_pair(qa, ha, rsa, rea, qb, hb, rsb, reb, ps, b.rk, g, bm, q, &s_tail, wbuf);
                 }
             }
             __syncthreads();
@@ -519,17 +497,23 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     if (lane == 0) c = atomicAdd(&s_hnext, 1u);
                     c = __shfl_sync(kFull, c, 0);
                     if (c >= nchunks) break;
-                    uint32_t lo = 0, hi = nh;  // s_hpre[lo] <= c < s_hpre[hi]
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (s_hpre[mid] <= c) lo = mid;
-                        else hi = mid;
+                    // owner: the last lo with s_hpre[lo] <= c, by a 32-way search
+                    // (invariant s_hpre[lo] <= c < s_hpre[lo + span]; lane 0's
+                    // probe is s_hpre[lo] itself, so the ballot is never empty)
+                    uint32_t lo = 0, span = nh;
+                    while (span > 1) {
+                        const uint32_t step = (span + 31) >> 5;
+                        const uint32_t off = (uint32_t)lane * step;
+                        const bool le = off < span && s_hpre[lo + off] <= c;
+                        const uint32_t t = 31 - __clz(__ballot_sync(kFull, le));
+                        lo += t * step;
+                        span = min(step, span - t * step);
                     }
                     uint32_t hrs, hre;
                     edge_range(g, s_hv[lo], hrs, hre);
                     const uint32_t q1 = (hre - 1) >> 2;
                     const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * kChunkQuads + lane;
-                    expand_pair(qa, qa <= q1, hrs, hre, qa + 32, qa + 32 <= q1, hrs, hre, s_lo, s_hi, key, g, bm, q,
+                    expand_pair(qa, qa <= q1, hrs, hre, qa + 32, qa + 32 <= q1, hrs, hre, ps, b.rk, g, bm, q,
                                 &s_tail, wbuf);
                 }
             }
@@ -653,10 +637,9 @@ lt_small_kernel(DevGraph g, SampleBatch b)
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31;
     const uint32_t ltm = lanemask_lt();
-    const uint2 key = philox_key(b.seed);
     bool busy = false, done = false;
     uint32_t rel = 0, len = 0, v = 0;
-    uint64_t s = 0;
+    PhiloxSet ps{};
     for (;;) {
         const uint32_t need = __ballot_sync(kFull, !busy && !done);
         if (need) {
@@ -669,8 +652,9 @@ lt_small_kernel(DevGraph g, SampleBatch b)
                 if (r < b.count) {
                     rel = r;
                     busy = true;
-                    s = b.base + rel;
-                    v = draw_root(b.seed, s, g.n);
+                    const uint64_t s = b.base + rel;
+                    ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
+                    v = draw_root(b.rk, s, g.n);
                     path[0][tid] = v;
                     len = 1;
                 } else {
@@ -681,7 +665,7 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         if (__all_sync(kFull, done)) break;
         if (!busy) continue;
         // one step of the reverse walk at v
-        const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), v, kTagLT), key);
+        const uint4 w = philox_x(v, ps, b.rk);
         uint32_t lo, hi;
         edge_range(g, v, lo, hi);
         const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8);
@@ -738,7 +722,6 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
     const int lane = threadIdx.x;
     uint32_t* bm = ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
-    const uint2 key = philox_key(b.seed);
     const uint32_t large_count = b.sc->large_count;
     const uint32_t words = b.words;
     for (;;) {
@@ -750,12 +733,13 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
         const uint64_t s = b.base + rel;
         uint32_t len = 0;
         if (lane == 0) {
-            uint32_t v = draw_root(b.seed, s, g.n);
+            const PhiloxSet ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
+            uint32_t v = draw_root(b.rk, s, g.n);
             q[0] = v;
             bm[v >> 5] |= 1u << (v & 31);
             len = 1;
             for (;;) {
-                const uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), v, kTagLT), key);
+                const uint4 w = philox_x(v, ps, b.rk);
                 uint32_t lo, hi;
                 edge_range(g, v, lo, hi);
                 const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8);

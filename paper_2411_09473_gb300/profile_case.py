@@ -48,11 +48,15 @@ def main():
         torch.cuda.synchronize()
         rec["s"] = time.perf_counter() - t0
         rec["sets"], rec["members"] = imm.imm_stream_size(ctx)
-        # in-edges examined = sum over members of their in-degree
+        # in-edges examined = sum over members of their in-degree; IC coin
+        # evaluations = (set, in-edge quad) pairs = sum over members of quads
         import numpy as np
         cnt = imm.imm_get_counts(ctx, g.n).astype(np.uint64)
-        indeg = np.diff(g.row.astype(np.int64)).astype(np.uint64)
+        row = g.row.astype(np.int64)
+        indeg = np.diff(row).astype(np.uint64)
         rec["edges"] = int((cnt * indeg).sum())
+        quads = np.where(indeg > 0, ((row[1:] - 1) >> 2) - (row[:-1] >> 2) + 1, 0).astype(np.uint64)
+        rec["quad_evals"] = int((cnt * quads).sum())
         out.append(rec)
     print(json.dumps(out))
     imm.imm_destroy(ctx)

@@ -17,6 +17,14 @@ pytestmark = pytest.mark.gpu
 IC, LT = graphgen.IC, graphgen.LT
 
 
+@pytest.fixture(params=["cta", "group"])
+def large_path(request, monkeypatch):
+    """IC sets that outgrow a warp go one per CTA, or 64 at a time through the
+    whole-GPU multi-source BFS; both must give the oracle's sets."""
+    monkeypatch.setenv("IMM_IC_LARGE", request.param)
+    return request.param
+
+
 @pytest.fixture(scope="module")
 def imm():
     import torch
@@ -89,7 +97,7 @@ def test_fuzz_small_graphs(imm, case):
 
 @pytest.mark.parametrize("n,m,gseed,pmax", [(3000, 24000, 11, 0.3), (1 << 14, 1 << 17, 12, 0.1),
                                             (5000, 20000, 13, 1.0)])
-def test_ic_rmat_giant_sets(imm, n, m, gseed, pmax):
+def test_ic_rmat_giant_sets(imm, large_path, n, m, gseed, pmax):
     # high edge probabilities: many sets outgrow a warp and go to the CTA path
     g = graphgen.make_graph(n, m, gseed, IC, "uniform", pmax=pmax)
     ctx = new_ctx(imm, g)
@@ -101,7 +109,7 @@ def test_ic_rmat_giant_sets(imm, n, m, gseed, pmax):
         assert np.array_equal(seeds, want) and cov == wcov
 
 
-def test_ic_p1_closures_and_star_hub(imm):
+def test_ic_p1_closures_and_star_hub(imm, large_path):
     # star: vertex 0 has 5000 in-neighbours, all with p = 1; every set rooted at 0
     # is the whole star (CTA path), the others are {leaf}
     n = 5001
@@ -138,7 +146,7 @@ def test_lt_long_walks(imm):
     check_stream(imm, ctx, cyc, 300, 3)
 
 
-def test_stream_extension_is_prefix_stable(imm):
+def test_stream_extension_is_prefix_stable(imm, large_path):
     g = graphgen.make_graph(2048, 16384, 21, IC, "uniform", pmax=0.2)
     a = new_ctx(imm, g)
     imm.imm_sample(a, IC, 100, 9)
@@ -151,7 +159,7 @@ def test_stream_extension_is_prefix_stable(imm):
     assert np.array_equal(imm.imm_get_counts(a, g.n), imm.imm_get_counts(b, g.n))
 
 
-def test_ic_global_bitmap_path(imm):
+def test_ic_global_bitmap_path(imm, large_path):
     # n = 2^21: the n-bit visited bitmap no longer fits in shared memory, so the
     # CTA path keeps it in a per-CTA global slot; compare sampled set ids
     n, m = 1 << 21, 1 << 23
@@ -170,6 +178,42 @@ def test_ic_global_bitmap_path(imm):
         want = o.sample_one(31, int(s))
         got = np.sort(mem[off[s]:off[s + 1]])
         assert np.array_equal(got, want), s
+
+
+def test_ic_group_ragged_groups_lists_and_bitmaps(imm, monkeypatch):
+    monkeypatch.setenv("IMM_IC_LARGE", "group")
+    # R-MAT with giant sets over several batches: groups of 64 and ragged
+    # last groups
+    g = graphgen.make_graph(1 << 13, 1 << 16, 41, IC, "uniform", pmax=0.25)
+    ctx = new_ctx(imm, g)
+    imm.imm_sample(ctx, IC, 300, 41)
+    check_stream(imm, ctx, g, 2600, 41)
+    off, _ = imm.imm_get_sets(ctx, 0, 2600)
+    assert (np.diff(off.astype(np.int64)) > 256).sum() > 130
+    # disjoint directed cycles with p = 1 in n = 2^15: a set rooted on a cycle
+    # is the whole cycle (one BFS level per member), stored as a list below
+    # n/32 = 1024 members and as a bitmap above; sparse random edges elsewhere
+    n = 1 << 15
+    lens = [300, 600, 900, 1500, 3000]
+    edges, base = [], 0
+    for ln in lens:
+        edges += [(base + i, base + (i + 1) % ln) for i in range(ln)]
+        base += ln
+    weights = [1.0] * len(edges)
+    rng = np.random.default_rng(5)
+    extra = set()
+    while len(extra) < 20000:
+        u, v = (int(x) for x in rng.integers(base, n, 2))
+        if u != v:
+            extra.add((u, v))
+    edges += sorted(extra)
+    weights += list(rng.uniform(0, 0.3, len(extra)))
+    cyc = edges_to_graph(n, edges, weights, IC)
+    ctx = new_ctx(imm, cyc)
+    check_stream(imm, ctx, cyc, 1500, 7)
+    off, _ = imm.imm_get_sets(ctx, 0, 1500)
+    sizes = set(np.diff(off.astype(np.int64)).tolist())
+    assert set(lens) <= sizes
 
 
 # ---------------------------------------------------------------------------
