@@ -90,11 +90,12 @@ __host__ __device__ __forceinline__ PhiloxSet philox_set(uint32_t s_lo, uint32_t
     return ps;
 }
 
-// philox((s_lo, s_hi, x, tag), key) for the set `ps` was built from.
-__host__ __device__ __forceinline__ uint4 philox_x(uint32_t x, const PhiloxSet& ps, const PhiloxKeys& rk)
+// philox((s_lo, s_hi, x, tag), key) for the set `ps` was built from, given
+// a = M1 * x (round 0's product of word 2, which is the same for every set:
+// sweeping many sets over one x computes it once).
+__host__ __device__ __forceinline__ uint4 philox_xa(uint64_t a, const PhiloxSet& ps, const PhiloxKeys& rk)
 {
     // round 0: only the product of word 2 (= x) depends on x
-    const uint64_t a = (uint64_t)kPhiloxM1 * (uint64_t)x;
     const uint32_t x0 = (uint32_t)(a >> 32) ^ ps.r0, x1 = (uint32_t)a;
     // round 1: counter (x0, x1, a2, a3); the product of a2 is in ps
     const uint64_t p = (uint64_t)kPhiloxM0 * (uint64_t)x0;
@@ -107,6 +108,11 @@ __host__ __device__ __forceinline__ uint4 philox_x(uint32_t x, const PhiloxSet& 
 #pragma unroll
     for (int r = 3; r < 10; ++r) c = philox_round(c, rk.k[2 * r], rk.k[2 * r + 1]);
     return c;
+}
+
+__host__ __device__ __forceinline__ uint4 philox_x(uint32_t x, const PhiloxSet& ps, const PhiloxKeys& rk)
+{
+    return philox_xa((uint64_t)kPhiloxM1 * (uint64_t)x, ps, rk);
 }
 
 // Root of set s: uniform over [0, n) by multiply-shift of a 64-bit draw.
@@ -243,12 +249,13 @@ cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const Devic
 cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
                            const DeviceInfo& di, cudaStream_t st);
 // Grouped IC large path: the large sets of a batch, 64 at a time, as one
-// multi-source BFS over the whole GPU (cooperative launch).
+// multi-source BFS over the whole GPU (cooperative launch), two groups in
+// flight (two slots of the arrays below).
 constexpr uint32_t kGroupSets = 64;
 struct GroupCounters {
     unsigned long long hpack[3];      // large frontier vertices << 40 | their chunks, by level mod 3
     uint32_t lcount[3];               // small frontier vertices, by level mod 3
-    uint32_t claim[3];                // work items claimed, by level mod 3
+    uint32_t claim[3];                // work items claimed, by step mod 3 (zero between launches)
     uint32_t cnt[kGroupSets];         // members per set
     uint32_t edges[kGroupSets];       // in-edges of the members per set
     uint32_t kind[kGroupSets];        // 0 list, 1 bitmap, 2 reservation failed
@@ -265,7 +272,8 @@ struct GroupScratch {
     uint32_t* hb1;            // [hcap] odd levels
     uint4* he0;               // [hcap] (v, rs, re, chunks left), even levels
     uint4* he1;               // [hcap] odd levels
-    GroupCounters* ctr;
+    uint64_t stride;          // bytes from each slot-0 array to its slot-1 twin
+    GroupCounters* ctr;       // [2], one per slot (ctr[0].claim serves both)
 };
 int ic_group_supported(const DeviceInfo& di);
 uint64_t ic_group_heavy_cap(uint32_t n, uint64_t m);

@@ -21,20 +21,24 @@
 // by the sets that reach v at the same level.
 //
 // A vertex is sorted when it is queued: vertices with >= 32 in-edge quads go
-// to a large list with a running chunk count, the others to a small list.  A
-// level is one grid-wide phase (cooperative launch, one 1024-thread CTA per
-// SM, a grid barrier between levels) in which warps claim work items from one
-// counter: first 32-vertex chunks of the small list, whose quads are
-// flattened across lanes (one quad per lane, its owner found from per-warp
-// run records in shared memory; up to 31 windows of 32 quads per item), then
-// the one-window 32-quad chunks of the large vertices (owner found by a
-// 32-way search over the chunk prefix), which even out the end of the level.
-// A large vertex's mask is merged into vis by the warp that sweeps its last
-// chunk.
+// to a large list with a running chunk count, the others to a small list.
+// The kernel is persistent (cooperative launch, one 1024-thread CTA per SM)
+// and advances in steps separated by grid barriers.  In a BFS step warps
+// claim work items from one counter: first 32-vertex chunks of the small
+// list, whose quads are flattened across lanes (one quad per lane, its owner
+// found from per-warp run records in shared memory; up to 31 windows of 32
+// quads per item), then the one-window 32-quad chunks of the large vertices
+// (owner found by a 32-way search over the chunk prefix), which even out the
+// end of the step.  A large vertex's mask is merged into vis by the warp that
+// sweeps its last chunk.
 //
 // When no frontier is left, two dense passes over vis give every set its
 // size and in-edge sum, reserve its output (member list, or an n-bit bitmap
 // when the list would be larger; Sec. IV-C), write it, and clear vis.
+//
+// Two groups are in flight, in two slots of the arrays: every step serves
+// both (their items share the counter), so one group's small levels, level
+// ends and extraction passes overlap the other group's big levels.
 #include "imm_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -45,11 +49,13 @@ namespace imm {
 
 namespace cg = cooperative_groups;
 
-constexpr int kGroupThreads = 1024;
+constexpr int kGroupThreads = 1024;  // threads per CTA
+constexpr int kGroupBlocks = 1;      // CTAs per SM (the cooperative grid is SMs x this)
+constexpr int kGroupChains = 2;      // independent Philox chains per lane in a sweep
 constexpr int kGroupWarps = kGroupThreads / 32;
 constexpr uint32_t kGroupHeavyQ = 32;  // in-edge quads from which a vertex is swept in 32-quad chunks
 constexpr unsigned long long kLow40 = (1ull << 40) - 1;
-constexpr uint32_t kHeavySmem = 8192;  // chunk prefix entries searched in shared memory
+constexpr uint32_t kHeavySmem = 6144;  // chunk prefix entries per slot searched in shared memory
 
 __device__ __forceinline__ uint32_t lanemask_le_g()
 {
@@ -83,25 +89,33 @@ struct QuadLive {
     uint4 src;  // tails of the four in-edges
 };
 
-// One half (32 sets) of the mask: coins of every set in `mask`, two sets per
-// step so that two independent Philox chains are in flight.
-__device__ __forceinline__ void sweep_half(uint32_t mask, uint32_t quad, uint4 tm, const PhiloxSet* ps,
+// One half (32 sets) of the mask: coins of every set in `mask` for the quad
+// whose round-0 product is `a`; with two chains, two sets per step so that
+// two independent Philox evaluations are in flight.
+__device__ __forceinline__ void sweep_half(uint32_t mask, uint64_t a, uint4 tm, const PhiloxSet* ps,
                                            const PhiloxKeys& rk, uint32_t* acc)
 {
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     while (mask) {
-        const int s1 = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const bool two = mask != 0;
-        const int s2 = two ? __ffs(mask) - 1 : s1;
-        if (two) mask &= mask - 1;
-        const uint32_t b1 = 1u << s1, b2 = two ? 1u << s2 : 0u;
-        const uint4 w1 = philox_x(quad, ps[s1], rk);
-        const uint4 w2 = philox_x(quad, ps[s2], rk);
-        a0 |= (w1.x <= tm.x ? b1 : 0u) | (w2.x <= tm.x ? b2 : 0u);
-        a1 |= (w1.y <= tm.y ? b1 : 0u) | (w2.y <= tm.y ? b2 : 0u);
-        a2 |= (w1.z <= tm.z ? b1 : 0u) | (w2.z <= tm.z ? b2 : 0u);
-        a3 |= (w1.w <= tm.w ? b1 : 0u) | (w2.w <= tm.w ? b2 : 0u);
+        const int s1 = 31 - __clz(mask);
+        mask ^= 1u << s1;
+        const uint32_t b1 = 1u << s1;
+        const uint4 w1 = philox_xa(a, ps[s1], rk);
+        if (kGroupChains == 2) {
+            const bool two = mask != 0;
+            const int s2 = two ? 31 - __clz(mask) : s1;
+            const uint32_t b2 = two ? 1u << s2 : 0u;
+            mask ^= b2;
+            const uint4 w2 = philox_xa(a, ps[s2], rk);
+            if (w2.x <= tm.x) a0 |= b2;
+            if (w2.y <= tm.y) a1 |= b2;
+            if (w2.z <= tm.z) a2 |= b2;
+            if (w2.w <= tm.w) a3 |= b2;
+        }
+        if (w1.x <= tm.x) a0 |= b1;
+        if (w1.y <= tm.y) a1 |= b1;
+        if (w1.z <= tm.z) a2 |= b1;
+        if (w1.w <= tm.w) a3 |= b1;
     }
     acc[0] = a0;
     acc[1] = a1;
@@ -125,8 +139,9 @@ __device__ __forceinline__ void sweep_quad(const DevGraph& g, const PhiloxKeys& 
     const uint32_t e0 = quad << 2;
     if (e0 < rs) valid &= 0xFu << (rs - e0);
     if (e0 + 4 > re) valid &= 0xFu >> (e0 + 4 - re);
-    sweep_half((uint32_t)F, quad, tm, ps, rk, ql.lo);
-    sweep_half((uint32_t)(F >> 32), quad, tm, ps + 32, rk, ql.hi);
+    const uint64_t a = (uint64_t)kPhiloxM1 * (uint64_t)quad;
+    sweep_half((uint32_t)F, a, tm, ps, rk, ql.lo);
+    sweep_half((uint32_t)(F >> 32), a, tm, ps + 32, rk, ql.hi);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         if (!((valid >> t) & 1u)) {
@@ -207,255 +222,390 @@ __device__ __forceinline__ void visit_quad(const DevGraph& g, const unsigned lon
         if (push[t]) o.lq[base++] = u[t];
 }
 
-__global__ void __launch_bounds__(kGroupThreads, 1)
+// Arrays of one group slot (slot 1's lie `stride` bytes after slot 0's).
+struct SlotArrays {
+    unsigned long long *vis, *fr0, *fr1;
+    uint32_t *lq0, *lq1, *hb0, *hb1;
+    uint4 *he0, *he1;
+    GroupCounters* ct;
+};
+
+__device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32_t k)
+{
+    const uint64_t d = k ? gs.stride : 0;
+    auto at = [d](auto* p) { return reinterpret_cast<decltype(p)>(reinterpret_cast<char*>(p) + d); };
+    SlotArrays a;
+    a.vis = at(gs.vis);
+    a.fr0 = at(gs.fr0);
+    a.fr1 = at(gs.fr1);
+    a.lq0 = at(gs.lq0);
+    a.lq1 = at(gs.lq1);
+    a.hb0 = at(gs.hb0);
+    a.hb1 = at(gs.hb1);
+    a.he0 = at(gs.he0);
+    a.he1 = at(gs.he1);
+    a.ct = gs.ctr + k;
+    return a;
+}
+
+// What a slot does in the current step (the same in every CTA: each CTA's
+// thread 0 advances its copy from the same global counters).
+constexpr uint32_t kIdle = 0, kInit = 1, kBfs = 2, kCount = 3, kReserve = 4, kWrite = 5;
+struct SlotStep {
+    uint32_t phase;
+    uint32_t level;  // BFS level being expanded (kBfs)
+    uint32_t g0, G;  // the group: large-queue entries g0 .. g0 + G - 1
+    uint32_t nl, nch, nh;  // small vertices, large-vertex chunks, large vertices of the level
+    uint32_t items;
+};
+constexpr uint32_t kWordsPerItem = 8;  // bitmap words per extraction item
+
+// One BFS level's view of a slot.
+struct LevelView {
+    const unsigned long long* fcur;
+    unsigned long long* fnext;
+    const uint32_t* lq;
+    const uint32_t* hb;
+    uint4* he;
+    LevelOut o;
+};
+
+__device__ __forceinline__ LevelView level_view(const SlotArrays& a, uint32_t level)
+{
+    const bool odd = level & 1u;
+    const uint32_t nxt = (level + 1) % 3;
+    LevelView v;
+    v.fcur = odd ? a.fr1 : a.fr0;
+    v.fnext = odd ? a.fr0 : a.fr1;
+    v.lq = odd ? a.lq1 : a.lq0;
+    v.hb = odd ? a.hb1 : a.hb0;
+    v.he = odd ? a.he1 : a.he0;
+    v.o = {&a.ct->hpack[nxt], &a.ct->lcount[nxt], odd ? a.lq0 : a.lq1, odd ? a.hb0 : a.hb1, odd ? a.he0 : a.he1};
+    return v;
+}
+
+// 32-quad chunk hc of the level's large vertices.  Owner: the last lo with
+// hb[lo] <= hc (invariant hb[lo] <= hc < hb[lo + span]; lane 0 probes lo
+// itself, so the ballot is never empty).
+__device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
+                                           const SlotArrays& a, const LevelView& lv, const uint32_t* s_hb,
+                                           bool hsm, uint32_t nh, uint32_t hc, uint32_t lane)
+{
+    uint32_t lo = 0, span = nh;
+    while (span > 1) {
+        const uint32_t step = (span + 31) >> 5;
+        const uint32_t off = lane * step;
+        const bool le = off < span && (hsm ? s_hb[lo + off] : __ldcg(lv.hb + lo + off)) <= hc;
+        const uint32_t t = 31 - __clz(__ballot_sync(kFull, le));
+        lo += t * step;
+        span = min(step, span - t * step);
+    }
+    const uint4 e = __ldcg(lv.he + lo);
+    const uint32_t first = hsm ? s_hb[lo] : __ldcg(lv.hb + lo);
+    const unsigned long long F = __ldcg(lv.fcur + e.x);
+    const uint32_t quad = (e.y >> 2) + (hc - first) * 32 + lane;
+    QuadLive ql = {};
+    if (quad <= ((e.z - 1) >> 2)) sweep_quad(g, rk, ps, quad, e.y, e.z, F, ql);
+    visit_quad(g, a.vis, lv.fcur, lv.fnext, lv.o, ql, lane);
+    // the warp that sweeps the vertex's last chunk merges its mask
+    if (lane == 0 && atomicSub(&lv.he[lo].w, 1u) == 1u) {
+        __stcg(a.vis + e.x, __ldcg(a.vis + e.x) | F);
+        __stcg(const_cast<unsigned long long*>(lv.fcur) + e.x, 0ull);
+    }
+}
+
+// 32 small vertices from lq[v0 ..): their quads flattened across lanes, in
+// windows of 32.  In a window, the run of each lane that meets it is
+// recorded at its first slot there; a slot's owner is the last recorded
+// start at or before it.
+__device__ __forceinline__ void small_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
+                                           const SlotArrays& a, const LevelView& lv, uint32_t nl, uint32_t v0,
+                                           uint4* rec, unsigned long long* recF, uint32_t lane)
+{
+    const uint32_t nf = min(nl - v0, 32u);
+    uint32_t rs = 0, re = 0, nq = 0;
+    unsigned long long F = 0;
+    if (lane < nf) {
+        const uint32_t v = __ldcg(lv.lq + v0 + lane);
+        F = __ldcg(lv.fcur + v);
+        __stcg(a.vis + v, __ldcg(a.vis + v) | F);
+        __stcg(const_cast<unsigned long long*>(lv.fcur) + v, 0ull);
+        range_of(g, v, rs, re);
+        nq = nquads(rs, re);
+    }
+    uint32_t incl = nq;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if ((int)lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - nq;
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        const bool meets = nq != 0 && excl < j0 + 32 && incl > j0;
+        const uint32_t st = excl > j0 ? excl - j0 : 0u;
+        if (meets) {
+            rec[st] = make_uint4(rs, re, excl, 0u);
+            recF[st] = F;
+        }
+        const uint32_t starts = __reduce_or_sync(kFull, meets ? 1u << st : 0u);
+        __syncwarp();
+        const uint32_t j = j0 + lane;
+        QuadLive ql = {};
+        if (j < total) {
+            const uint32_t pos = 31 - __clz(starts & lanemask_le_g());
+            const uint4 r = rec[pos];
+            const uint32_t quad = (r.x >> 2) + (j - r.z);
+            sweep_quad(g, rk, ps, quad, r.x, r.y, recF[pos], ql);
+        }
+        visit_quad(g, a.vis, lv.fcur, lv.fnext, lv.o, ql, lane);
+        __syncwarp();
+    }
+}
+
+// Count pass over words [w0, w0 + kWordsPerItem): members and in-edge sums
+// of the group's sets, into the CTA's shared accumulators.
+__device__ __forceinline__ void count_item(const DevGraph& g, const SlotArrays& a, uint32_t G, uint32_t words,
+                                           uint32_t w0, uint32_t* s_cnt, uint32_t* s_edg, uint32_t lane)
+{
+    const uint32_t w1 = min(w0 + kWordsPerItem, words);
+    for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t u = (w << 5) + lane;
+        const unsigned long long m = u < g.n ? __ldcg(a.vis + u) : 0ull;
+        if (!__any_sync(kFull, m != 0ull)) continue;
+        uint32_t d = 0;
+        if (m) {
+            uint32_t rs, re;
+            range_of(g, u, rs, re);
+            d = re - rs;
+        }
+        for (uint32_t s = 0; s < G; ++s) {
+            const bool in = (m >> s) & 1ull;
+            const uint32_t bal = __ballot_sync(kFull, in);
+            if (bal) {
+                const uint32_t e = __reduce_add_sync(kFull, in ? d : 0u);
+                if (lane == 0) {
+                    atomicAdd(&s_cnt[s], (uint32_t)__popc(bal));
+                    atomicAdd(&s_edg[s], e);
+                }
+            }
+        }
+    }
+}
+
+// Write pass over words [w0, w0 + kWordsPerItem): member lists and bitmap
+// words of the group's sets; clears vis.
+__device__ __forceinline__ void write_item(const DevGraph& g, const SampleBatch& b, const SlotArrays& a,
+                                           uint32_t G, uint32_t words, uint32_t w0, const uint32_t* s_kind,
+                                           const unsigned long long* s_pos, uint32_t lane)
+{
+    const uint32_t w1 = min(w0 + kWordsPerItem, words);
+    for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t u = (w << 5) + lane;
+        unsigned long long m = 0;
+        if (u < g.n) {
+            m = __ldcg(a.vis + u);
+            if (m) __stcg(a.vis + u, 0ull);
+        }
+        uint32_t mine0 = 0, mine1 = 0;  // bitmap word w of sets lane and lane + 32
+        if (__any_sync(kFull, m != 0ull)) {
+            for (uint32_t s = 0; s < G; ++s) {
+                const bool in = (m >> s) & 1ull;
+                const uint32_t bal = __ballot_sync(kFull, in);
+                if (lane == (s & 31)) {
+                    if (s < 32) mine0 = bal;
+                    else mine1 = bal;
+                }
+                if (bal && s_kind[s] == 0) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = (uint32_t)atomicAdd(&a.ct->lcur[s], (unsigned long long)__popc(bal));
+                    base = __shfl_sync(kFull, base, 0);
+                    if (in) b.big[s_pos[s] + base + __popc(bal & lanemask_lt_g())] = u;
+                }
+            }
+        }
+        if (lane < G && s_kind[lane] == 1) b.big[s_pos[lane] + w] = mine0;
+        if (lane + 32 < G && s_kind[lane + 32] == 1) b.big[s_pos[lane + 32] + w] = mine1;
+    }
+}
+
+// Two groups are in flight: a step (between grid barriers) serves both
+// slots, so one group's small levels, level ends and extraction passes
+// overlap the other's big levels.
+__global__ void __launch_bounds__(kGroupThreads, kGroupBlocks)
 ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
 {
-    extern __shared__ uint32_t s_hbase[];  // [kHeavySmem] copy of the level's chunk prefix
-    __shared__ PhiloxSet s_ps[kGroupSets];
+    extern __shared__ uint32_t s_hbase[];  // [2][kHeavySmem] copies of the levels' chunk prefixes
+    __shared__ PhiloxSet s_ps[2][kGroupSets];
     __shared__ uint4 s_rec[kGroupWarps][32];                // run records: rs, re, first slot
     __shared__ unsigned long long s_recF[kGroupWarps][32];  // run records: frontier mask
-    __shared__ uint32_t s_cnt[kGroupSets], s_edg[kGroupSets], s_kind[kGroupSets];
-    __shared__ unsigned long long s_pos[kGroupSets];
+    __shared__ uint32_t s_cnt[2][kGroupSets], s_edg[2][kGroupSets], s_kind[2][kGroupSets];
+    __shared__ unsigned long long s_pos[2][kGroupSets];
+    __shared__ SlotStep s_st[2];
+    __shared__ uint32_t s_next;
 
     cg::grid_group grid = cg::this_grid();
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31, wid = tid >> 5;
-    const uint32_t gwarp = blockIdx.x * kGroupWarps + wid;
-    const uint32_t nwarps = gridDim.x * kGroupWarps;
     const uint32_t large_count = b.sc->large_count;  // final: written by the previous launch
     const uint32_t words = b.words;
-    GroupCounters* ct = gs.ctr;
+    const uint32_t witems = (words + kWordsPerItem - 1) / kWordsPerItem;
+    uint32_t* claim = gs.ctr[0].claim;
 
-    for (uint32_t g0 = 0; g0 < large_count; g0 += kGroupSets) {
-        const uint32_t G = min(kGroupSets, large_count - g0);
-        if (tid < G) {
-            const uint64_t s = b.base + b.large_q[g0 + tid];
-            s_ps[tid] = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagIC, b.rk);
-        }
-        if (blockIdx.x == 0) {
-            if (tid < 3) {
-                ct->hpack[tid] = 0;
-                ct->lcount[tid] = 0;
-                ct->claim[tid] = 0;
-            }
-            if (tid < kGroupSets) {
-                ct->cnt[tid] = 0;
-                ct->edges[tid] = 0;
-                ct->lcur[tid] = 0;
-            }
-            __syncthreads();
-            if (tid < G) {
-                const uint64_t s = b.base + b.large_q[g0 + tid];
-                const uint32_t root = draw_root(b.rk, s, g.n);
-                if (atomicOr(gs.fr0 + root, 1ull << tid) == 0ull) {
-                    const LevelOut o = {&ct->hpack[0], &ct->lcount[0], gs.lq0, gs.hb0, gs.he0};
-                    uint32_t rs, re;
-                    range_of(g, root, rs, re);
-                    if (queue_large(o, root, rs, re)) gs.lq0[atomicAdd(&ct->lcount[0], 1u)] = root;
+    if (tid == 0) {
+        s_st[0].phase = kIdle;
+        s_st[1].phase = kIdle;
+        s_next = 0;
+    }
+    for (uint32_t step = 0;; ++step) {
+        // ---- advance both slots (thread 0 of every CTA, same inputs)
+        if (tid == 0) {
+            for (uint32_t k = 0; k < 2; ++k) {
+                SlotStep& v = s_st[k];
+                const GroupCounters* ct = gs.ctr + k;
+                if (v.phase == kBfs) ++v.level;
+                else if (v.phase == kInit) {
+                    v.phase = kBfs;
+                    v.level = 0;
+                } else if (v.phase == kCount) v.phase = kReserve;
+                else if (v.phase == kReserve) v.phase = kWrite;
+                else if (v.phase == kWrite) v.phase = kIdle;
+                if (v.phase == kBfs) {
+                    const uint32_t cur = v.level % 3;
+                    const unsigned long long hp = __ldcg(&ct->hpack[cur]);
+                    v.nh = (uint32_t)(hp >> 40);
+                    v.nch = (uint32_t)(hp & kLow40);
+                    v.nl = __ldcg(&ct->lcount[cur]);
+                    if (v.nch == 0 && v.nl == 0) v.phase = kCount;
                 }
+                if (v.phase == kIdle && s_next < large_count) {
+                    v.phase = kInit;
+                    v.g0 = s_next;
+                    v.G = min(kGroupSets, large_count - s_next);
+                    s_next += kGroupSets;
+                }
+                v.items = v.phase == kBfs ? (v.nl + 31) / 32 + v.nch
+                                          : (v.phase == kCount || v.phase == kWrite ? witems : 0u);
             }
         }
-        grid.sync();
+        __syncthreads();
+        if (s_st[0].phase == kIdle && s_st[1].phase == kIdle) {
+            // every CTA is past the last barrier: leave the claim counters
+            // zero for the next launch
+            if (blockIdx.x == 0 && tid < 3) claim[tid] = 0;
+            break;
+        }
 
-        for (uint32_t lvl = 0;; ++lvl) {
-            const uint32_t cur = lvl % 3, nxt = (lvl + 1) % 3;
-            const bool odd = lvl & 1u;
-            const unsigned long long hp = __ldcg(&ct->hpack[cur]);
-            const uint32_t nh = (uint32_t)(hp >> 40), nch = (uint32_t)(hp & kLow40);
-            const uint32_t nl = __ldcg(&ct->lcount[cur]);
-            if (nch == 0 && nl == 0) break;
-            if (blockIdx.x == 0 && tid == 0) {
-                // counters of the level before this one: read by everybody
-                // before the last barrier; they serve the level after next
-                const uint32_t old = (lvl + 2) % 3;
-                ct->hpack[old] = 0;
-                ct->lcount[old] = 0;
-                ct->claim[old] = 0;
-            }
-            const unsigned long long* fcur = odd ? gs.fr1 : gs.fr0;
-            unsigned long long* fnext = odd ? gs.fr0 : gs.fr1;
-            const uint32_t* lq = odd ? gs.lq1 : gs.lq0;
-            const uint32_t* hb = odd ? gs.hb1 : gs.hb0;
-            uint4* he = odd ? gs.he1 : gs.he0;
-            const LevelOut o = {&ct->hpack[nxt], &ct->lcount[nxt], odd ? gs.lq0 : gs.lq1, odd ? gs.hb0 : gs.hb1,
-                                odd ? gs.he0 : gs.he1};
-            const bool hsm = nh <= kHeavySmem;
-            if (hsm)
-                for (uint32_t i = tid; i < nh; i += kGroupThreads) s_hbase[i] = __ldcg(hb + i);
-            __syncthreads();
-
-            // items: 32-vertex chunks of the small list first (the longest
-            // items: up to 31 windows each), then 32-quad chunks of the large
-            // vertices (one window each), which even out the end of the level
-            const uint32_t nlc = (nl + 31) / 32;
-            const uint32_t items = nlc + nch;
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(&ct->claim[cur], 1u);
-            c = __shfl_sync(kFull, c, 0);
-            while (c < items) {
-                uint32_t cn = 0;  // the next claim, in flight while this item runs
-                if (lane == 0) cn = atomicAdd(&ct->claim[cur], 1u);
-                if (c >= nlc) {
-                    // ---- 32-quad chunk of a large vertex; owner: the last lo
-                    // with hb[lo] <= c (invariant hb[lo] <= c < hb[lo + span];
-                    // lane 0 probes lo itself, so the ballot is never empty)
-                    const uint32_t hc = c - nlc;
-                    uint32_t lo = 0, span = nh;
-                    while (span > 1) {
-                        const uint32_t step = (span + 31) >> 5;
-                        const uint32_t off = lane * step;
-                        const bool le = off < span && (hsm ? s_hbase[lo + off] : __ldcg(hb + lo + off)) <= hc;
-                        const uint32_t t = 31 - __clz(__ballot_sync(kFull, le));
-                        lo += t * step;
-                        span = min(step, span - t * step);
+        // ---- per-CTA preparation of each slot's step
+        if (blockIdx.x == 0 && tid == 0) claim[(step + 2) % 3] = 0;  // the step before this one's
+        for (uint32_t k = 0; k < 2; ++k) {
+            const SlotStep v = s_st[k];
+            const SlotArrays a = slot_arrays(gs, k);
+            if (v.phase == kInit) {
+                if (tid < v.G) {
+                    const uint64_t s = b.base + b.large_q[v.g0 + tid];
+                    s_ps[k][tid] = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagIC, b.rk);
+                }
+                if (blockIdx.x == 0) {
+                    if (tid < 3) {
+                        a.ct->hpack[tid] = 0;
+                        a.ct->lcount[tid] = 0;
                     }
-                    const uint4 e = __ldcg(he + lo);
-                    const uint32_t first = hsm ? s_hbase[lo] : __ldcg(hb + lo);
-                    const unsigned long long F = __ldcg(fcur + e.x);
-                    const uint32_t quad = (e.y >> 2) + (hc - first) * 32 + lane;
-                    QuadLive ql = {};
-                    if (quad <= ((e.z - 1) >> 2)) sweep_quad(g, b.rk, s_ps, quad, e.y, e.z, F, ql);
-                    visit_quad(g, gs.vis, fcur, fnext, o, ql, lane);
-                    // the warp that sweeps the vertex's last chunk merges its mask
-                    if (lane == 0 && atomicSub(&he[lo].w, 1u) == 1u) {
-                        __stcg(gs.vis + e.x, __ldcg(gs.vis + e.x) | F);
-                        __stcg(const_cast<unsigned long long*>(fcur) + e.x, 0ull);
+                    if (tid < kGroupSets) {
+                        a.ct->cnt[tid] = 0;
+                        a.ct->edges[tid] = 0;
+                        a.ct->lcur[tid] = 0;
                     }
-                } else {
-                    // ---- 32 small vertices: quads flattened across lanes
-                    const uint32_t v0 = c * 32;
-                    const uint32_t nf = min(nl - v0, 32u);
-                    uint32_t rs = 0, re = 0, nq = 0;
-                    unsigned long long F = 0;
-                    if (lane < nf) {
-                        const uint32_t v = __ldcg(lq + v0 + lane);
-                        F = __ldcg(fcur + v);
-                        __stcg(gs.vis + v, __ldcg(gs.vis + v) | F);
-                        __stcg(const_cast<unsigned long long*>(fcur) + v, 0ull);
-                        range_of(g, v, rs, re);
-                        nq = nquads(rs, re);
-                    }
-                    uint32_t incl = nq;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t t = __shfl_up_sync(kFull, incl, d);
-                        if ((int)lane >= d) incl += t;
-                    }
-                    const uint32_t total = __shfl_sync(kFull, incl, 31);
-                    const uint32_t excl = incl - nq;
-                    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-                        // the run of each lane that meets slots [j0, j0 + 32) is
-                        // recorded at its first slot there; a slot's owner is the
-                        // last recorded start at or before it
-                        const bool meets = nq != 0 && excl < j0 + 32 && incl > j0;
-                        const uint32_t st = excl > j0 ? excl - j0 : 0u;
-                        if (meets) {
-                            s_rec[wid][st] = make_uint4(rs, re, excl, 0u);
-                            s_recF[wid][st] = F;
+                    __syncthreads();
+                    if (tid < v.G) {
+                        const uint64_t s = b.base + b.large_q[v.g0 + tid];
+                        const uint32_t root = draw_root(b.rk, s, g.n);
+                        if (atomicOr(a.fr0 + root, 1ull << tid) == 0ull) {
+                            const LevelOut o = {&a.ct->hpack[0], &a.ct->lcount[0], a.lq0, a.hb0, a.he0};
+                            uint32_t rs, re;
+                            range_of(g, root, rs, re);
+                            if (queue_large(o, root, rs, re)) a.lq0[atomicAdd(&a.ct->lcount[0], 1u)] = root;
                         }
-                        const uint32_t starts = __reduce_or_sync(kFull, meets ? 1u << st : 0u);
-                        __syncwarp();
-                        const uint32_t j = j0 + lane;
-                        QuadLive ql = {};
-                        if (j < total) {
-                            const uint32_t pos = 31 - __clz(starts & lanemask_le_g());
-                            const uint4 r = s_rec[wid][pos];
-                            const uint32_t quad = (r.x >> 2) + (j - r.z);
-                            sweep_quad(g, b.rk, s_ps, quad, r.x, r.y, s_recF[wid][pos], ql);
-                        }
-                        visit_quad(g, gs.vis, fcur, fnext, o, ql, lane);
-                        __syncwarp();
                     }
                 }
-                c = __shfl_sync(kFull, cn, 0);
+            } else if (v.phase == kBfs) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    // counters of the level before this one: read by everybody
+                    // before the last barrier; they serve the level after next
+                    const uint32_t old = (v.level + 2) % 3;
+                    a.ct->hpack[old] = 0;
+                    a.ct->lcount[old] = 0;
+                }
+                if (v.nh <= kHeavySmem) {
+                    const uint32_t* hb = (v.level & 1u) ? a.hb1 : a.hb0;
+                    for (uint32_t i = tid; i < v.nh; i += kGroupThreads) s_hbase[k * kHeavySmem + i] = __ldcg(hb + i);
+                }
+            } else if (v.phase == kCount) {
+                if (tid < kGroupSets) {
+                    s_cnt[k][tid] = 0;
+                    s_edg[k][tid] = 0;
+                }
+            } else if (v.phase == kReserve) {
+                if (blockIdx.x == 0 && tid < v.G) {
+                    const uint32_t rel = b.large_q[v.g0 + tid];
+                    const uint32_t len = __ldcg(&a.ct->cnt[tid]);
+                    b.set_edges[rel] = __ldcg(&a.ct->edges[tid]);
+                    const uint32_t kind = len > words ? 1u : 0u;
+                    uint64_t pos = 0;
+                    const bool ok = reserve_big(b, rel, len, kind, &pos);
+                    a.ct->kind[tid] = ok ? kind : 2u;
+                    a.ct->pos[tid] = pos;
+                }
+            } else if (v.phase == kWrite) {
+                if (tid < v.G) {
+                    s_kind[k][tid] = __ldcg(&a.ct->kind[tid]);
+                    s_pos[k][tid] = __ldcg(&a.ct->pos[tid]);
+                }
             }
-            grid.sync();
         }
+        __syncthreads();
 
-        // ---- sizes and in-edge sums of the group's sets
-        if (tid < kGroupSets) {
-            s_cnt[tid] = 0;
-            s_edg[tid] = 0;
+        // ---- work items of both slots from one counter
+        const uint32_t i0 = s_st[0].items, total = i0 + s_st[1].items;
+        uint32_t* cl = claim + step % 3;
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(cl, 1u);
+        c = __shfl_sync(kFull, c, 0);
+        while (c < total) {
+            uint32_t cn = 0;  // the next claim, in flight while this item runs
+            if (lane == 0) cn = atomicAdd(cl, 1u);
+            const uint32_t k = c < i0 ? 0u : 1u;
+            const uint32_t ci = c - (k ? i0 : 0u);
+            const SlotStep& v = s_st[k];
+            const SlotArrays a = slot_arrays(gs, k);
+            if (v.phase == kBfs) {
+                const LevelView lv = level_view(a, v.level);
+                const uint32_t nlc = (v.nl + 31) / 32;
+                // small-vertex chunks first (up to 31 windows each), then the
+                // one-window chunks of the large vertices
+                if (ci < nlc) small_item(g, b.rk, s_ps[k], a, lv, v.nl, ci * 32, s_rec[wid], s_recF[wid], lane);
+                else large_item(g, b.rk, s_ps[k], a, lv, s_hbase + k * kHeavySmem, v.nh <= kHeavySmem, v.nh,
+                                ci - nlc, lane);
+            } else if (v.phase == kCount) {
+                count_item(g, a, v.G, words, ci * kWordsPerItem, s_cnt[k], s_edg[k], lane);
+            } else {
+                write_item(g, b, a, v.G, words, ci * kWordsPerItem, s_kind[k], s_pos[k], lane);
+            }
+            c = __shfl_sync(kFull, cn, 0);
         }
         __syncthreads();
-        for (uint32_t w = gwarp; w < words; w += nwarps) {
-            const uint32_t u = (w << 5) + lane;
-            const unsigned long long m = u < g.n ? __ldcg(gs.vis + u) : 0ull;
-            if (!__any_sync(kFull, m != 0ull)) continue;
-            uint32_t d = 0;
-            if (m) {
-                uint32_t rs, re;
-                range_of(g, u, rs, re);
-                d = re - rs;
+        for (uint32_t k = 0; k < 2; ++k) {
+            if (s_st[k].phase == kCount && tid < s_st[k].G) {
+                GroupCounters* ct = gs.ctr + k;
+                atomicAdd(&ct->cnt[tid], s_cnt[k][tid]);
+                atomicAdd(&ct->edges[tid], s_edg[k][tid]);
             }
-            for (uint32_t s = 0; s < G; ++s) {
-                const bool in = (m >> s) & 1ull;
-                const uint32_t bal = __ballot_sync(kFull, in);
-                if (bal) {
-                    const uint32_t e = __reduce_add_sync(kFull, in ? d : 0u);
-                    if (lane == 0) {
-                        atomicAdd(&s_cnt[s], (uint32_t)__popc(bal));
-                        atomicAdd(&s_edg[s], e);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (tid < G) {
-            atomicAdd(&ct->cnt[tid], s_cnt[tid]);
-            atomicAdd(&ct->edges[tid], s_edg[tid]);
-        }
-        grid.sync();
-        if (blockIdx.x == 0 && tid < G) {
-            const uint32_t rel = b.large_q[g0 + tid];
-            const uint32_t len = __ldcg(&ct->cnt[tid]);
-            b.set_edges[rel] = __ldcg(&ct->edges[tid]);
-            const uint32_t kind = len > words ? 1u : 0u;
-            uint64_t pos = 0;
-            const bool ok = reserve_big(b, rel, len, kind, &pos);
-            ct->kind[tid] = ok ? kind : 2u;
-            ct->pos[tid] = pos;
-        }
-        grid.sync();
-
-        // ---- write member lists / bitmaps, clear vis
-        if (tid < G) {
-            s_kind[tid] = __ldcg(&ct->kind[tid]);
-            s_pos[tid] = __ldcg(&ct->pos[tid]);
-        }
-        __syncthreads();
-        for (uint32_t w = gwarp; w < words; w += nwarps) {
-            const uint32_t u = (w << 5) + lane;
-            unsigned long long m = 0;
-            if (u < g.n) {
-                m = __ldcg(gs.vis + u);
-                if (m) __stcg(gs.vis + u, 0ull);
-            }
-            uint32_t mine0 = 0, mine1 = 0;  // bitmap word w of sets lane and lane + 32
-            if (__any_sync(kFull, m != 0ull)) {
-                for (uint32_t s = 0; s < G; ++s) {
-                    const bool in = (m >> s) & 1ull;
-                    const uint32_t bal = __ballot_sync(kFull, in);
-                    if (lane == (s & 31)) {
-                        if (s < 32) mine0 = bal;
-                        else mine1 = bal;
-                    }
-                    if (bal && s_kind[s] == 0) {
-                        uint32_t base = 0;
-                        if (lane == 0) base = (uint32_t)atomicAdd(&ct->lcur[s], (unsigned long long)__popc(bal));
-                        base = __shfl_sync(kFull, base, 0);
-                        if (in) b.big[s_pos[s] + base + __popc(bal & lanemask_lt_g())] = u;
-                    }
-                }
-            }
-            if (lane < G && s_kind[lane] == 1) b.big[s_pos[lane] + w] = mine0;
-            if (lane + 32 < G && s_kind[lane + 32] == 1) b.big[s_pos[lane + 32] + w] = mine1;
         }
         grid.sync();
     }
 }
 
-constexpr size_t kGroupDynSmem = kHeavySmem * 4;
+constexpr size_t kGroupDynSmem = 2 * kHeavySmem * 4;
 
 int ic_group_supported(const DeviceInfo& di)
 {
@@ -467,7 +617,7 @@ int ic_group_supported(const DeviceInfo& di)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ic_group_kernel, kGroupThreads, kGroupDynSmem) !=
         cudaSuccess)
         return 0;
-    return per_sm >= 1 ? 1 : 0;
+    return per_sm >= kGroupBlocks ? 1 : 0;
 }
 
 uint64_t ic_group_heavy_cap(uint32_t n, uint64_t m)
@@ -483,8 +633,8 @@ cudaError_t launch_ic_group(const DevGraph& g, const SampleBatch& b, const Group
     SampleBatch ba = b;
     GroupScratch sa = gs;
     void* args[] = {&ga, &ba, &sa};
-    return cudaLaunchCooperativeKernel((const void*)ic_group_kernel, dim3((unsigned)di.sms), dim3(kGroupThreads),
-                                       args, kGroupDynSmem, st);
+    return cudaLaunchCooperativeKernel((const void*)ic_group_kernel, dim3((unsigned)(di.sms * kGroupBlocks)),
+                                       dim3(kGroupThreads), args, kGroupDynSmem, st);
 }
 
 }  // namespace imm
