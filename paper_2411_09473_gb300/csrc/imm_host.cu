@@ -405,31 +405,25 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     const uint64_t n = c->n;
     const uint64_t hcap = ic_group_heavy_cap(c->n, c->m);
     auto up = [](uint64_t x) { return (x + 255) & ~255ull; };
-    // one slot: masks (zeroed once; every launch leaves them zero), lists
-    const uint64_t o_fr0 = up(n * 8), o_fr1 = o_fr0 + up(n * 8), o_lq0 = o_fr1 + up(n * 8);
-    const uint64_t o_lq1 = o_lq0 + up(n * 4), o_hb0 = o_lq1 + up(n * 4), o_hb1 = o_hb0 + up(hcap * 4);
-    const uint64_t o_he0 = o_hb1 + up(hcap * 4), o_he1 = o_he0 + up(hcap * 16);
-    const uint64_t slot = o_he1 + up(hcap * 16);
+    // one slot: vis and fn (zeroed once; every launch leaves them zero), lists
+    const uint64_t o_fn = up(n * 8), o_lq = o_fn + up(n * 8), o_hb = o_lq + up(n * 16);
+    const uint64_t o_he = o_hb + up(hcap * 4), slot = o_he + up(hcap * 16);
     const uint64_t o_ct = 2 * slot;
     const uint64_t bytes = o_ct + up(2 * sizeof(GroupCounters));
     char* p;
     if (c->grp.bytes < bytes) {
         TRY(dalloc(c, c->grp, bytes));
         p = static_cast<char*>(c->grp.p);
-        CK(cudaMemsetAsync(p, 0, o_lq0, c->stream));
-        CK(cudaMemsetAsync(p + slot, 0, o_lq0, c->stream));
+        CK(cudaMemsetAsync(p, 0, o_lq, c->stream));
+        CK(cudaMemsetAsync(p + slot, 0, o_lq, c->stream));
         CK(cudaMemsetAsync(p + o_ct, 0, 2 * sizeof(GroupCounters), c->stream));
     }
     p = static_cast<char*>(c->grp.p);
     gs->vis = reinterpret_cast<unsigned long long*>(p);
-    gs->fr0 = reinterpret_cast<unsigned long long*>(p + o_fr0);
-    gs->fr1 = reinterpret_cast<unsigned long long*>(p + o_fr1);
-    gs->lq0 = reinterpret_cast<uint32_t*>(p + o_lq0);
-    gs->lq1 = reinterpret_cast<uint32_t*>(p + o_lq1);
-    gs->hb0 = reinterpret_cast<uint32_t*>(p + o_hb0);
-    gs->hb1 = reinterpret_cast<uint32_t*>(p + o_hb1);
-    gs->he0 = reinterpret_cast<uint4*>(p + o_he0);
-    gs->he1 = reinterpret_cast<uint4*>(p + o_he1);
+    gs->fn = reinterpret_cast<unsigned long long*>(p + o_fn);
+    gs->lq = reinterpret_cast<uint4*>(p + o_lq);
+    gs->hb = reinterpret_cast<uint32_t*>(p + o_hb);
+    gs->he = reinterpret_cast<uint4*>(p + o_he);
     gs->stride = slot;
     gs->ctr = reinterpret_cast<GroupCounters*>(p + o_ct);
     return IMM_OK;

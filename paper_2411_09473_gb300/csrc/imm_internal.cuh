@@ -253,8 +253,8 @@ cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeS
 // flight (two slots of the arrays below).
 constexpr uint32_t kGroupSets = 64;
 struct GroupCounters {
-    unsigned long long hpack[3];      // large frontier vertices << 40 | their chunks, by level mod 3
-    uint32_t lcount[3];               // small frontier vertices, by level mod 3
+    unsigned long long hpack[2];      // listed large vertices << 40 | their chunks, by level parity
+    uint32_t lcount[2];               // listed small vertices, by level parity
     uint32_t claim[3];                // work items claimed, by step mod 3 (zero between launches)
     uint32_t cnt[kGroupSets];         // members per set
     uint32_t edges[kGroupSets];       // in-edges of the members per set
@@ -264,14 +264,10 @@ struct GroupCounters {
 };
 struct GroupScratch {
     unsigned long long* vis;  // [n] sets of the group that expanded v (zero between groups)
-    unsigned long long* fr0;  // [n] frontier masks, even levels (zero outside the frontier)
-    unsigned long long* fr1;  // [n] odd levels
-    uint32_t* lq0;            // [n] small frontier vertices, even levels
-    uint32_t* lq1;            // [n] odd levels
-    uint32_t* hb0;            // [hcap] first chunk of each large frontier vertex, even levels
-    uint32_t* hb1;            // [hcap] odd levels
-    uint4* he0;               // [hcap] (v, rs, re, chunks left), even levels
-    uint4* he1;               // [hcap] odd levels
+    unsigned long long* fn;   // [n] sets that reached v in the level being expanded (zero otherwise)
+    uint4* lq;                // [n] small vertices of the level: (rs, re, F lo, F hi)
+    uint32_t* hb;             // [hcap] first chunk of each large vertex of the level
+    uint4* he;                // [hcap] large vertices: (rs, re, F lo, F hi)
     uint64_t stride;          // bytes from each slot-0 array to its slot-1 twin
     GroupCounters* ctr;       // [2], one per slot (ctr[0].claim serves both)
 };

@@ -2,43 +2,44 @@
 // time by the whole GPU as one multi-source reverse BFS (Generate_RRRsets,
 // EfficientIMM Alg. 3, for many roots at once).
 //
-// Each vertex carries three 64-bit masks over the sets of the group: vis (the
-// sets whose BFS has expanded it) and the frontier masks of the current and
-// the next level.  Level by level, a frontier vertex v with mask F adds F to
-// vis[v], reads its in-edge thresholds and sources once and flips the coins
-// of every set in F: in-edge e = (u -> v) of set s is live iff word e&3 of
-// Philox(s, e>>2) passes e's threshold (the same draw as the one-set-per-CTA
-// path, so every set equals the reverse-reachable closure of its root under
-// its own coins, whatever the traversal order).  Live bits that u holds
-// neither in vis[u] nor in its current-frontier mask are ored into u's
-// next-frontier mask, and u is queued for the next level when that mask
-// leaves zero.  A visit that races with u's own expansion may see neither
-// mask updated and queue bits u already expands; u then sweeps them once more
-// with no effect on any set (the sets are read from vis), so the race costs
-// work, never correctness.  The giant sets of a power-law graph walk the same
-// high-degree core within a level or two of each other, so the per-vertex
-// work (edge range, threshold and source loads, quad bookkeeping) is shared
-// by the sets that reach v at the same level.
+// Each vertex carries two 64-bit masks over the sets of the group: vis (the
+// sets that reached it in earlier levels) and fn (the sets that reached it in
+// the level being expanded).  A level takes two steps:
+//   expand  every vertex v of the level, with its new sets F, reads its
+//           in-edge thresholds and sources once and flips the coins of every
+//           set in F: in-edge e = (u -> v) of set s is live iff word e&3 of
+//           Philox(s, e>>2) passes e's threshold (the same draw as the
+//           one-set-per-CTA path, so every set is the reverse-reachable
+//           closure of its root under its own coins, whatever the traversal
+//           order).  Live bits u lacks in vis[u] are ored into fn[u], with no
+//           value returned.
+//   scan    a dense pass over fn merges every nonzero fn[v] into vis[v],
+//           clears it and lists v with F = fn[v] for the next expansion:
+//           vertices with >= 32 in-edge quads in a large list with a running
+//           chunk count, the others in a small list.
+// vis changes only in scan steps, so expansions read it without races.  The
+// giant sets of a power-law graph walk the same high-degree core within a
+// level or two of each other, so the per-vertex work (edge range, threshold
+// and source loads, quad bookkeeping) is shared by the sets that reach v at
+// the same level.
 //
-// A vertex is sorted when it is queued: vertices with >= 32 in-edge quads go
-// to a large list with a running chunk count, the others to a small list.
 // The kernel is persistent (cooperative launch, one 1024-thread CTA per SM)
-// and advances in steps separated by grid barriers.  In a BFS step warps
-// claim work items from one counter: first 32-vertex chunks of the small
-// list, whose quads are flattened across lanes (one quad per lane, its owner
-// found from per-warp run records in shared memory; up to 31 windows of 32
-// quads per item), then the one-window 32-quad chunks of the large vertices
-// (owner found by a 32-way search over the chunk prefix), which even out the
-// end of the step.  A large vertex's mask is merged into vis by the warp that
-// sweeps its last chunk.
+// and advances in steps separated by grid barriers; warps claim work items
+// from one counter.  Expansion items are 32-vertex chunks of the small list,
+// whose quads are flattened across lanes (one quad per lane, its owner found
+// from per-warp run records in shared memory; up to 31 windows of 32 quads
+// per item), and one-window 32-quad chunks of the large vertices (owner found
+// by a 32-way search over the chunk prefix).
 //
-// When no frontier is left, two dense passes over vis give every set its
+// When no vertex is listed, two dense passes over vis give every set its
 // size and in-edge sum, reserve its output (member list, or an n-bit bitmap
 // when the list would be larger; Sec. IV-C), write it, and clear vis.
 //
-// Two groups are in flight, in two slots of the arrays: every step serves
-// both (their items share the counter), so one group's small levels, level
-// ends and extraction passes overlap the other group's big levels.
+// Two groups are in flight, in two slots of the arrays, the second started a
+// few steps after the first: every step serves both (long items of both
+// first, then the one-window chunks, which even out the end of the step), so
+// one group's small levels, scans and extraction passes overlap the other
+// group's big levels.
 #include "imm_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -151,37 +152,12 @@ __device__ __forceinline__ void sweep_quad(const DevGraph& g, const PhiloxKeys& 
     }
 }
 
-// Where a level's visits queue the next frontier.
-struct LevelOut {
-    unsigned long long* hpack;  // large vertices << 40 | their chunks
-    uint32_t* lcount;           // small vertices
-    uint32_t* lq;               // small vertex ids
-    uint32_t* hb;               // first chunk of each large vertex
-    uint4* he;                  // large vertices: (v, rs, re, chunks not yet swept)
-};
-
-// Sort a vertex that just entered the next frontier into the large or small
-// list; returns true when it went to the small list (queued by the caller).
-__device__ __forceinline__ bool queue_large(const LevelOut& o, uint32_t u, uint32_t rs, uint32_t re)
-{
-    const uint32_t nq = nquads(rs, re);
-    if (nq < kGroupHeavyQ) return true;
-    const uint32_t nch = (nq + 31) >> 5;
-    const unsigned long long old = atomicAdd(o.hpack, (1ull << 40) | (unsigned long long)nch);
-    const uint32_t i = (uint32_t)(old >> 40);
-    o.hb[i] = (uint32_t)(old & kLow40);
-    o.he[i] = make_uint4(u, rs, re, nch);
-    return false;
-}
-
-// Apply the live bits of one quad per lane: bits u neither expanded nor has
-// in the current frontier go to u's next-frontier mask; u is queued when that
-// mask leaves zero.  Every lane's four lookups, then its four atomics, are
-// independent, so each step costs one memory round trip.  Called by the
-// whole warp.
-__device__ __forceinline__ void visit_quad(const DevGraph& g, const unsigned long long* vis,
-                                           const unsigned long long* fcur, unsigned long long* fnext,
-                                           const LevelOut& o, const QuadLive& ql, uint32_t lane)
+// Apply the live bits of one quad per lane: bits u has not been expanded for
+// are ored into fn[u] (no value returned: nothing waits on it).  The four
+// lookups of a lane are independent, so the visit costs one memory round
+// trip.
+__device__ __forceinline__ void visit_quad(const unsigned long long* vis, unsigned long long* fn,
+                                           const QuadLive& ql)
 {
     const uint32_t u[4] = {ql.src.x, ql.src.y, ql.src.z, ql.src.w};
     unsigned long long m[4];
@@ -189,44 +165,19 @@ __device__ __forceinline__ void visit_quad(const DevGraph& g, const unsigned lon
     for (int t = 0; t < 4; ++t) m[t] = ((unsigned long long)ql.hi[t] << 32) | ql.lo[t];
     unsigned long long known[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) known[t] = m[t] ? __ldcg(vis + u[t]) | __ldcg(fcur + u[t]) : ~0ull;
-    bool push[4];
+    for (int t = 0; t < 4; ++t) known[t] = m[t] ? __ldcg(vis + u[t]) : ~0ull;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         m[t] &= ~known[t];
-        push[t] = m[t] ? atomicOr(fnext + u[t], m[t]) == 0ull : false;
+        if (m[t]) atomicOr(fn + u[t], m[t]);
     }
-    uint32_t np = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        if (push[t]) {
-            uint32_t rs, re;
-            range_of(g, u[t], rs, re);
-            push[t] = queue_large(o, u[t], rs, re);
-            np += push[t] ? 1u : 0u;
-        }
-    }
-    uint32_t incl = np;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t x = __shfl_up_sync(kFull, incl, d);
-        if ((int)lane >= d) incl += x;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return;
-    uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(o.lcount, total);
-    base = __shfl_sync(kFull, base, 31) + incl - np;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-        if (push[t]) o.lq[base++] = u[t];
 }
 
 // Arrays of one group slot (slot 1's lie `stride` bytes after slot 0's).
 struct SlotArrays {
-    unsigned long long *vis, *fr0, *fr1;
-    uint32_t *lq0, *lq1, *hb0, *hb1;
-    uint4 *he0, *he1;
+    unsigned long long *vis, *fn;
+    uint4 *lq, *he;
+    uint32_t* hb;
     GroupCounters* ct;
 };
 
@@ -236,103 +187,110 @@ __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32
     auto at = [d](auto* p) { return reinterpret_cast<decltype(p)>(reinterpret_cast<char*>(p) + d); };
     SlotArrays a;
     a.vis = at(gs.vis);
-    a.fr0 = at(gs.fr0);
-    a.fr1 = at(gs.fr1);
-    a.lq0 = at(gs.lq0);
-    a.lq1 = at(gs.lq1);
-    a.hb0 = at(gs.hb0);
-    a.hb1 = at(gs.hb1);
-    a.he0 = at(gs.he0);
-    a.he1 = at(gs.he1);
+    a.fn = at(gs.fn);
+    a.lq = at(gs.lq);
+    a.he = at(gs.he);
+    a.hb = at(gs.hb);
     a.ct = gs.ctr + k;
     return a;
 }
 
+// Enter a vertex with new bits F into the level's lists: vertices with >= 32
+// in-edge quads go to the large list (chunk prefix in hb), the others to the
+// small list (collected per warp by the caller; returns true for those).
+__device__ __forceinline__ bool list_large(const SlotArrays& a, uint32_t par, uint32_t rs, uint32_t re,
+                                           unsigned long long F)
+{
+    const uint32_t nq = nquads(rs, re);
+    if (nq < kGroupHeavyQ) return true;
+    const unsigned long long old =
+        atomicAdd(&a.ct->hpack[par], (1ull << 40) | (unsigned long long)((nq + 31) >> 5));
+    const uint32_t i = (uint32_t)(old >> 40);
+    a.hb[i] = (uint32_t)(old & kLow40);
+    a.he[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
+    return false;
+}
+
 // What a slot does in the current step (the same in every CTA: each CTA's
 // thread 0 advances its copy from the same global counters).
-constexpr uint32_t kIdle = 0, kInit = 1, kBfs = 2, kCount = 3, kReserve = 4, kWrite = 5;
+constexpr uint32_t kIdle = 0, kInit = 1, kScan = 2, kExpand = 3, kCount = 4, kReserve = 5, kWrite = 6;
 struct SlotStep {
     uint32_t phase;
-    uint32_t level;  // BFS level being expanded (kBfs)
-    uint32_t g0, G;  // the group: large-queue entries g0 .. g0 + G - 1
-    uint32_t nl, nch, nh;  // small vertices, large-vertex chunks, large vertices of the level
-    uint32_t items;
+    uint32_t level;        // BFS level listed (kScan) or expanded (kExpand)
+    uint32_t g0, G;        // the group: large-queue entries g0 .. g0 + G - 1
+    uint32_t nl, nch, nh;  // kExpand: small vertices, large-vertex chunks, large vertices
+    uint32_t nlong, nshort;  // work items: long ones first, then one-window chunks
 };
-constexpr uint32_t kWordsPerItem = 8;  // bitmap words per extraction item
+constexpr uint32_t kWordsPerItem = 8;     // bitmap words per extraction item
+constexpr uint32_t kScanPerItem = 256;    // vertices per scan item
+constexpr uint32_t kSlotOffset = 6;       // steps by which slot 1 starts after slot 0
 
-// One BFS level's view of a slot.
-struct LevelView {
-    const unsigned long long* fcur;
-    unsigned long long* fnext;
-    const uint32_t* lq;
-    const uint32_t* hb;
-    uint4* he;
-    LevelOut o;
-};
-
-__device__ __forceinline__ LevelView level_view(const SlotArrays& a, uint32_t level)
+// Scan of vertices [v0, v0 + kScanPerItem): every vertex with new bits F has
+// them merged into vis, cleared from fn and is listed for expansion.
+__device__ __forceinline__ void scan_item(const DevGraph& g, const SlotArrays& a, uint32_t par, uint32_t v0,
+                                          uint32_t lane)
 {
-    const bool odd = level & 1u;
-    const uint32_t nxt = (level + 1) % 3;
-    LevelView v;
-    v.fcur = odd ? a.fr1 : a.fr0;
-    v.fnext = odd ? a.fr0 : a.fr1;
-    v.lq = odd ? a.lq1 : a.lq0;
-    v.hb = odd ? a.hb1 : a.hb0;
-    v.he = odd ? a.he1 : a.he0;
-    v.o = {&a.ct->hpack[nxt], &a.ct->lcount[nxt], odd ? a.lq0 : a.lq1, odd ? a.hb0 : a.hb1, odd ? a.he0 : a.he1};
-    return v;
+    const uint32_t ltm = lanemask_lt_g();
+    for (uint32_t r = 0; r < kScanPerItem; r += 32) {
+        const uint32_t v = v0 + r + lane;
+        const unsigned long long F = v < g.n ? __ldcg(a.fn + v) : 0ull;
+        if (!__any_sync(kFull, F != 0ull)) continue;
+        bool small = false;
+        uint32_t rs = 0, re = 0;
+        if (F) {
+            __stcg(a.fn + v, 0ull);
+            __stcg(a.vis + v, __ldcg(a.vis + v) | F);
+            range_of(g, v, rs, re);
+            small = list_large(a, par, rs, re, F);
+        }
+        const uint32_t bal = __ballot_sync(kFull, small);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(&a.ct->lcount[par], (uint32_t)__popc(bal));
+            base = __shfl_sync(kFull, base, leader);
+            if (small) a.lq[base + __popc(bal & ltm)] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
+        }
+    }
 }
 
 // 32-quad chunk hc of the level's large vertices.  Owner: the last lo with
 // hb[lo] <= hc (invariant hb[lo] <= hc < hb[lo + span]; lane 0 probes lo
 // itself, so the ballot is never empty).
 __device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
-                                           const SlotArrays& a, const LevelView& lv, const uint32_t* s_hb,
-                                           bool hsm, uint32_t nh, uint32_t hc, uint32_t lane)
+                                           const SlotArrays& a, const uint32_t* s_hb, bool hsm, uint32_t nh,
+                                           uint32_t hc, uint32_t lane)
 {
     uint32_t lo = 0, span = nh;
     while (span > 1) {
         const uint32_t step = (span + 31) >> 5;
         const uint32_t off = lane * step;
-        const bool le = off < span && (hsm ? s_hb[lo + off] : __ldcg(lv.hb + lo + off)) <= hc;
+        const bool le = off < span && (hsm ? s_hb[lo + off] : __ldcg(a.hb + lo + off)) <= hc;
         const uint32_t t = 31 - __clz(__ballot_sync(kFull, le));
         lo += t * step;
         span = min(step, span - t * step);
     }
-    const uint4 e = __ldcg(lv.he + lo);
-    const uint32_t first = hsm ? s_hb[lo] : __ldcg(lv.hb + lo);
-    const unsigned long long F = __ldcg(lv.fcur + e.x);
-    const uint32_t quad = (e.y >> 2) + (hc - first) * 32 + lane;
+    const uint4 e = __ldcg(a.he + lo);
+    const uint32_t first = hsm ? s_hb[lo] : __ldcg(a.hb + lo);
+    const uint32_t quad = (e.x >> 2) + (hc - first) * 32 + lane;
     QuadLive ql = {};
-    if (quad <= ((e.z - 1) >> 2)) sweep_quad(g, rk, ps, quad, e.y, e.z, F, ql);
-    visit_quad(g, a.vis, lv.fcur, lv.fnext, lv.o, ql, lane);
-    // the warp that sweeps the vertex's last chunk merges its mask
-    if (lane == 0 && atomicSub(&lv.he[lo].w, 1u) == 1u) {
-        __stcg(a.vis + e.x, __ldcg(a.vis + e.x) | F);
-        __stcg(const_cast<unsigned long long*>(lv.fcur) + e.x, 0ull);
-    }
+    if (quad <= ((e.y - 1) >> 2))
+        sweep_quad(g, rk, ps, quad, e.x, e.y, ((unsigned long long)e.w << 32) | e.z, ql);
+    visit_quad(a.vis, a.fn, ql);
 }
 
-// 32 small vertices from lq[v0 ..): their quads flattened across lanes, in
+// 32 small vertices from lq[i0 ..): their quads flattened across lanes, in
 // windows of 32.  In a window, the run of each lane that meets it is
 // recorded at its first slot there; a slot's owner is the last recorded
 // start at or before it.
 __device__ __forceinline__ void small_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
-                                           const SlotArrays& a, const LevelView& lv, uint32_t nl, uint32_t v0,
-                                           uint4* rec, unsigned long long* recF, uint32_t lane)
+                                           const SlotArrays& a, uint32_t nl, uint32_t i0, uint4* rec,
+                                           unsigned long long* recF, uint32_t lane)
 {
-    const uint32_t nf = min(nl - v0, 32u);
-    uint32_t rs = 0, re = 0, nq = 0;
-    unsigned long long F = 0;
-    if (lane < nf) {
-        const uint32_t v = __ldcg(lv.lq + v0 + lane);
-        F = __ldcg(lv.fcur + v);
-        __stcg(a.vis + v, __ldcg(a.vis + v) | F);
-        __stcg(const_cast<unsigned long long*>(lv.fcur) + v, 0ull);
-        range_of(g, v, rs, re);
-        nq = nquads(rs, re);
-    }
+    const uint32_t nf = min(nl - i0, 32u);
+    uint4 e = make_uint4(0, 0, 0, 0);
+    if (lane < nf) e = __ldcg(a.lq + i0 + lane);
+    const uint32_t nq = nquads(e.x, e.y);
     uint32_t incl = nq;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -345,8 +303,8 @@ __device__ __forceinline__ void small_item(const DevGraph& g, const PhiloxKeys& 
         const bool meets = nq != 0 && excl < j0 + 32 && incl > j0;
         const uint32_t st = excl > j0 ? excl - j0 : 0u;
         if (meets) {
-            rec[st] = make_uint4(rs, re, excl, 0u);
-            recF[st] = F;
+            rec[st] = make_uint4(e.x, e.y, excl, 0u);
+            recF[st] = ((unsigned long long)e.w << 32) | e.z;
         }
         const uint32_t starts = __reduce_or_sync(kFull, meets ? 1u << st : 0u);
         __syncwarp();
@@ -358,7 +316,7 @@ __device__ __forceinline__ void small_item(const DevGraph& g, const PhiloxKeys& 
             const uint32_t quad = (r.x >> 2) + (j - r.z);
             sweep_quad(g, rk, ps, quad, r.x, r.y, recF[pos], ql);
         }
-        visit_quad(g, a.vis, lv.fcur, lv.fnext, lv.o, ql, lane);
+        visit_quad(a.vis, a.fn, ql);
         __syncwarp();
     }
 }
@@ -429,16 +387,13 @@ __device__ __forceinline__ void write_item(const DevGraph& g, const SampleBatch&
     }
 }
 
-// Two groups are in flight: a step (between grid barriers) serves both
-// slots, so one group's small levels, level ends and extraction passes
-// overlap the other's big levels.
 __global__ void __launch_bounds__(kGroupThreads, kGroupBlocks)
 ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
 {
     extern __shared__ uint32_t s_hbase[];  // [2][kHeavySmem] copies of the levels' chunk prefixes
     __shared__ PhiloxSet s_ps[2][kGroupSets];
     __shared__ uint4 s_rec[kGroupWarps][32];                // run records: rs, re, first slot
-    __shared__ unsigned long long s_recF[kGroupWarps][32];  // run records: frontier mask
+    __shared__ unsigned long long s_recF[kGroupWarps][32];  // run records: new bits
     __shared__ uint32_t s_cnt[2][kGroupSets], s_edg[2][kGroupSets], s_kind[2][kGroupSets];
     __shared__ unsigned long long s_pos[2][kGroupSets];
     __shared__ SlotStep s_st[2];
@@ -450,6 +405,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
     const uint32_t large_count = b.sc->large_count;  // final: written by the previous launch
     const uint32_t words = b.words;
     const uint32_t witems = (words + kWordsPerItem - 1) / kWordsPerItem;
+    const uint32_t sitems = (g.n + kScanPerItem - 1) / kScanPerItem;
     uint32_t* claim = gs.ctr[0].claim;
 
     if (tid == 0) {
@@ -463,33 +419,44 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
             for (uint32_t k = 0; k < 2; ++k) {
                 SlotStep& v = s_st[k];
                 const GroupCounters* ct = gs.ctr + k;
-                if (v.phase == kBfs) ++v.level;
-                else if (v.phase == kInit) {
-                    v.phase = kBfs;
+                const uint32_t was = v.phase;
+                if (was == kInit) {
+                    v.phase = kExpand;
                     v.level = 0;
-                } else if (v.phase == kCount) v.phase = kReserve;
-                else if (v.phase == kReserve) v.phase = kWrite;
-                else if (v.phase == kWrite) v.phase = kIdle;
-                if (v.phase == kBfs) {
-                    const uint32_t cur = v.level % 3;
-                    const unsigned long long hp = __ldcg(&ct->hpack[cur]);
+                } else if (was == kScan) {
+                    v.phase = kExpand;
+                } else if (was == kExpand) {
+                    v.phase = kScan;
+                    ++v.level;
+                } else if (was == kCount) {
+                    v.phase = kReserve;
+                } else if (was == kReserve) {
+                    v.phase = kWrite;
+                } else if (was == kWrite) {
+                    v.phase = kIdle;
+                }
+                if (v.phase == kExpand) {
+                    const uint32_t par = v.level & 1u;
+                    const unsigned long long hp = __ldcg(&ct->hpack[par]);
                     v.nh = (uint32_t)(hp >> 40);
                     v.nch = (uint32_t)(hp & kLow40);
-                    v.nl = __ldcg(&ct->lcount[cur]);
+                    v.nl = __ldcg(&ct->lcount[par]);
                     if (v.nch == 0 && v.nl == 0) v.phase = kCount;
                 }
-                if (v.phase == kIdle && s_next < large_count) {
+                if (v.phase == kIdle && s_next < large_count && (k == 0 || step >= kSlotOffset)) {
                     v.phase = kInit;
                     v.g0 = s_next;
                     v.G = min(kGroupSets, large_count - s_next);
                     s_next += kGroupSets;
                 }
-                v.items = v.phase == kBfs ? (v.nl + 31) / 32 + v.nch
-                                          : (v.phase == kCount || v.phase == kWrite ? witems : 0u);
+                v.nlong = v.phase == kExpand ? (v.nl + 31) / 32
+                        : v.phase == kScan ? sitems
+                        : (v.phase == kCount || v.phase == kWrite) ? witems : 0u;
+                v.nshort = v.phase == kExpand ? v.nch : 0u;
             }
         }
         __syncthreads();
-        if (s_st[0].phase == kIdle && s_st[1].phase == kIdle) {
+        if (s_st[0].phase == kIdle && s_st[1].phase == kIdle && s_next >= large_count) {
             // every CTA is past the last barrier: leave the claim counters
             // zero for the next launch
             if (blockIdx.x == 0 && tid < 3) claim[tid] = 0;
@@ -507,7 +474,8 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                     s_ps[k][tid] = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagIC, b.rk);
                 }
                 if (blockIdx.x == 0) {
-                    if (tid < 3) {
+                    // level 0: the roots, listed directly
+                    if (tid < 2) {
                         a.ct->hpack[tid] = 0;
                         a.ct->lcount[tid] = 0;
                     }
@@ -516,30 +484,35 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                         a.ct->edges[tid] = 0;
                         a.ct->lcur[tid] = 0;
                     }
-                    __syncthreads();
+                    uint32_t root = 0;
+                    bool first = false;
                     if (tid < v.G) {
                         const uint64_t s = b.base + b.large_q[v.g0 + tid];
-                        const uint32_t root = draw_root(b.rk, s, g.n);
-                        if (atomicOr(a.fr0 + root, 1ull << tid) == 0ull) {
-                            const LevelOut o = {&a.ct->hpack[0], &a.ct->lcount[0], a.lq0, a.hb0, a.he0};
-                            uint32_t rs, re;
-                            range_of(g, root, rs, re);
-                            if (queue_large(o, root, rs, re)) a.lq0[atomicAdd(&a.ct->lcount[0], 1u)] = root;
-                        }
+                        root = draw_root(b.rk, s, g.n);
+                        first = atomicOr(a.fn + root, 1ull << tid) == 0ull;
+                    }
+                    __syncthreads();
+                    if (first) {
+                        const unsigned long long F = __ldcg(a.fn + root);
+                        __stcg(a.fn + root, 0ull);
+                        __stcg(a.vis + root, F);
+                        uint32_t rs, re;
+                        range_of(g, root, rs, re);
+                        if (list_large(a, 0, rs, re, F))
+                            a.lq[atomicAdd(&a.ct->lcount[0], 1u)] =
+                                make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
                     }
                 }
-            } else if (v.phase == kBfs) {
+            } else if (v.phase == kExpand) {
                 if (blockIdx.x == 0 && tid == 0) {
-                    // counters of the level before this one: read by everybody
-                    // before the last barrier; they serve the level after next
-                    const uint32_t old = (v.level + 2) % 3;
-                    a.ct->hpack[old] = 0;
-                    a.ct->lcount[old] = 0;
+                    // the next scan's counters: last read at the top of the
+                    // previous expansion step
+                    const uint32_t np = (v.level + 1) & 1u;
+                    a.ct->hpack[np] = 0;
+                    a.ct->lcount[np] = 0;
                 }
-                if (v.nh <= kHeavySmem) {
-                    const uint32_t* hb = (v.level & 1u) ? a.hb1 : a.hb0;
-                    for (uint32_t i = tid; i < v.nh; i += kGroupThreads) s_hbase[k * kHeavySmem + i] = __ldcg(hb + i);
-                }
+                if (v.nh <= kHeavySmem)
+                    for (uint32_t i = tid; i < v.nh; i += kGroupThreads) s_hbase[k * kHeavySmem + i] = __ldcg(a.hb + i);
             } else if (v.phase == kCount) {
                 if (tid < kGroupSets) {
                     s_cnt[k][tid] = 0;
@@ -565,8 +538,10 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
         }
         __syncthreads();
 
-        // ---- work items of both slots from one counter
-        const uint32_t i0 = s_st[0].items, total = i0 + s_st[1].items;
+        // ---- work items of both slots from one counter: the long items of
+        // both slots first, then the one-window chunks (they even out the end)
+        const uint32_t l0 = s_st[0].nlong, l1 = s_st[1].nlong, h0 = s_st[0].nshort;
+        const uint32_t total = l0 + l1 + h0 + s_st[1].nshort;
         uint32_t* cl = claim + step % 3;
         uint32_t c = 0;
         if (lane == 0) c = atomicAdd(cl, 1u);
@@ -574,18 +549,20 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
         while (c < total) {
             uint32_t cn = 0;  // the next claim, in flight while this item runs
             if (lane == 0) cn = atomicAdd(cl, 1u);
-            const uint32_t k = c < i0 ? 0u : 1u;
-            const uint32_t ci = c - (k ? i0 : 0u);
+            uint32_t k, ci;
+            bool lng;
+            if (c < l0) { k = 0; ci = c; lng = true; }
+            else if (c < l0 + l1) { k = 1; ci = c - l0; lng = true; }
+            else if (c < l0 + l1 + h0) { k = 0; ci = c - l0 - l1; lng = false; }
+            else { k = 1; ci = c - l0 - l1 - h0; lng = false; }
             const SlotStep& v = s_st[k];
             const SlotArrays a = slot_arrays(gs, k);
-            if (v.phase == kBfs) {
-                const LevelView lv = level_view(a, v.level);
-                const uint32_t nlc = (v.nl + 31) / 32;
-                // small-vertex chunks first (up to 31 windows each), then the
-                // one-window chunks of the large vertices
-                if (ci < nlc) small_item(g, b.rk, s_ps[k], a, lv, v.nl, ci * 32, s_rec[wid], s_recF[wid], lane);
-                else large_item(g, b.rk, s_ps[k], a, lv, s_hbase + k * kHeavySmem, v.nh <= kHeavySmem, v.nh,
-                                ci - nlc, lane);
+            if (!lng) {
+                large_item(g, b.rk, s_ps[k], a, s_hbase + k * kHeavySmem, v.nh <= kHeavySmem, v.nh, ci, lane);
+            } else if (v.phase == kExpand) {
+                small_item(g, b.rk, s_ps[k], a, v.nl, ci * 32, s_rec[wid], s_recF[wid], lane);
+            } else if (v.phase == kScan) {
+                scan_item(g, a, v.level & 1u, ci * kScanPerItem, lane);
             } else if (v.phase == kCount) {
                 count_item(g, a, v.G, words, ci * kWordsPerItem, s_cnt[k], s_edg[k], lane);
             } else {
