@@ -42,9 +42,9 @@ METRIC = "IMM seconds-to-seeds"
 # xors = 40 instructions) and 4 threshold compares, against the issue rate of
 # the GPU (SMs x 4 schedulers x 32 lanes x max SM clock).
 ALU_OPS_PER_QUAD_EVAL = 44
-# DRAM bytes per quad evaluation of the dominant IC kernel, from one ncu capture
-# (profiles/ic_group_kernel__ic_u01_1m_first2000sets.md); None until captured.
-IC_DRAM_BYTES_PER_QUAD_EVAL = 3.565422e9 / 1192743275
+# DRAM bytes per quad evaluation of the dominant IC kernel on the 1M-vertex
+# workload, from one ncu capture (profiles/ic_group_kernel__ic_u01_1m_first2000sets.md)
+IC_DRAM_BYTES_PER_QUAD_EVAL = 3.509548e9 / 1192743275
 WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "batch64", "served")
 
 
@@ -337,7 +337,7 @@ def run_gpu(args, dist: Dist):
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "peak_kind": f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz",
                 "traffic": (IC_DRAM_BYTES_PER_QUAD_EVAL * evals / max(launches, 1)
-                            if IC_DRAM_BYTES_PER_QUAD_EVAL else None),
+                            if args.workload == "ic_u01_1m" else None),
                 "traffic_source": "ncu dram__bytes_read+write per quad evaluation of the dominant kernel, "
                                   "scaled to the average timed launch",
                 "algorithmic_ops": f"{ALU_OPS_PER_QUAD_EVAL} integer instructions per (set, in-edge quad) "
