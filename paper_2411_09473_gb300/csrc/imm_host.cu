@@ -406,7 +406,10 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     const uint64_t hcap = ic_group_heavy_cap(c->n, c->m);
     auto up = [](uint64_t x) { return (x + 255) & ~255ull; };
     // one slot: vis and fn (zeroed once; every launch leaves them zero), lists
-    const uint64_t o_fn = up(n * 8), o_lq = o_fn + up(n * 8), o_hb = o_lq + up(n * 16);
+    // windows of 32 small quads per level: a vertex has at most (indeg + 6) / 4 quads
+    const uint64_t wcap = (c->m + 6 * n) / 128 + 2;
+    const uint64_t o_fn = up(n * 8), o_lq = o_fn + up(n * 8), o_lpre = o_lq + up(n * 16);
+    const uint64_t o_wst = o_lpre + up(n * 4), o_hb = o_wst + up(wcap * 4);
     const uint64_t o_he = o_hb + up(hcap * 4), slot = o_he + up(hcap * 16);
     const uint64_t o_ct = 2 * slot;
     const uint64_t bytes = o_ct + up(2 * sizeof(GroupCounters));
@@ -422,6 +425,8 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     gs->vis = reinterpret_cast<unsigned long long*>(p);
     gs->fn = reinterpret_cast<unsigned long long*>(p + o_fn);
     gs->lq = reinterpret_cast<uint4*>(p + o_lq);
+    gs->lpre = reinterpret_cast<uint32_t*>(p + o_lpre);
+    gs->wst = reinterpret_cast<uint32_t*>(p + o_wst);
     gs->hb = reinterpret_cast<uint32_t*>(p + o_hb);
     gs->he = reinterpret_cast<uint4*>(p + o_he);
     gs->stride = slot;

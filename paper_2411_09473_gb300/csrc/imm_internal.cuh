@@ -253,8 +253,8 @@ cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeS
 // flight (two slots of the arrays below).
 constexpr uint32_t kGroupSets = 64;
 struct GroupCounters {
-    unsigned long long hpack[2];      // listed large vertices << 40 | their chunks, by level parity
-    uint32_t lcount[2];               // listed small vertices, by level parity
+    unsigned long long hpack[2];      // listed large vertices << 36 | their chunks, by level parity
+    unsigned long long lpack[2];      // listed small vertices << 36 | their quads, by level parity
     uint32_t claim[3];                // work items claimed, by step mod 3 (zero between launches)
     uint32_t cnt[kGroupSets];         // members per set
     uint32_t edges[kGroupSets];       // in-edges of the members per set
@@ -266,6 +266,8 @@ struct GroupScratch {
     unsigned long long* vis;  // [n] sets of the group that expanded v (zero between groups)
     unsigned long long* fn;   // [n] sets that reached v in the level being expanded (zero otherwise)
     uint4* lq;                // [n] small vertices of the level: (rs, re, F lo, F hi)
+    uint32_t* lpre;           // [n] their offsets in the level's small quads
+    uint32_t* wst;            // [wcap] first small entry of each 32-quad window
     uint32_t* hb;             // [hcap] first chunk of each large vertex of the level
     uint4* he;                // [hcap] large vertices: (rs, re, F lo, F hi)
     uint64_t stride;          // bytes from each slot-0 array to its slot-1 twin

@@ -55,7 +55,9 @@ constexpr int kGroupBlocks = 1;      // CTAs per SM (the cooperative grid is SMs
 constexpr int kGroupChains = 2;      // independent Philox chains per lane in a sweep
 constexpr int kGroupWarps = kGroupThreads / 32;
 constexpr uint32_t kGroupHeavyQ = 32;  // in-edge quads from which a vertex is swept in 32-quad chunks
-constexpr unsigned long long kLow40 = (1ull << 40) - 1;
+// packed list counters: entries << 36 | quads (small list) or chunks (large list)
+constexpr int kPackShift = 36;
+constexpr unsigned long long kPackLow = (1ull << kPackShift) - 1;
 constexpr uint32_t kHeavySmem = 6144;  // chunk prefix entries per slot searched in shared memory
 
 __device__ __forceinline__ uint32_t lanemask_le_g()
@@ -177,7 +179,7 @@ __device__ __forceinline__ void visit_quad(const unsigned long long* vis, unsign
 struct SlotArrays {
     unsigned long long *vis, *fn;
     uint4 *lq, *he;
-    uint32_t* hb;
+    uint32_t *lpre, *wst, *hb;
     GroupCounters* ct;
 };
 
@@ -190,25 +192,36 @@ __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32
     a.fn = at(gs.fn);
     a.lq = at(gs.lq);
     a.he = at(gs.he);
+    a.lpre = at(gs.lpre);
+    a.wst = at(gs.wst);
     a.hb = at(gs.hb);
     a.ct = gs.ctr + k;
     return a;
 }
 
-// Enter a vertex with new bits F into the level's lists: vertices with >= 32
-// in-edge quads go to the large list (chunk prefix in hb), the others to the
-// small list (collected per warp by the caller; returns true for those).
-__device__ __forceinline__ bool list_large(const SlotArrays& a, uint32_t par, uint32_t rs, uint32_t re,
-                                           unsigned long long F)
+// A vertex with >= 32 in-edge quads and new bits F enters the level's large
+// list (32-quad chunks; chunk prefix in hb).
+__device__ __forceinline__ void list_large(const SlotArrays& a, uint32_t par, uint32_t rs, uint32_t re,
+                                           uint32_t nq, unsigned long long F)
 {
-    const uint32_t nq = nquads(rs, re);
-    if (nq < kGroupHeavyQ) return true;
     const unsigned long long old =
-        atomicAdd(&a.ct->hpack[par], (1ull << 40) | (unsigned long long)((nq + 31) >> 5));
-    const uint32_t i = (uint32_t)(old >> 40);
-    a.hb[i] = (uint32_t)(old & kLow40);
+        atomicAdd(&a.ct->hpack[par], (1ull << kPackShift) | (unsigned long long)((nq + 31) >> 5));
+    const uint32_t i = (uint32_t)(old >> kPackShift);
+    a.hb[i] = (uint32_t)(old & kPackLow);
     a.he[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
-    return false;
+}
+
+// Small-list entry i of a vertex with 1..31 in-edge quads at quad offset off
+// of the level's small quads.  The windows of 32 quads that the expansion
+// sweeps start at multiples of 32; the one window start inside
+// [off, off + nq), if any, records i as that window's first entry.
+__device__ __forceinline__ void list_small(const SlotArrays& a, uint32_t i, uint32_t off, uint32_t rs,
+                                           uint32_t re, uint32_t nq, unsigned long long F)
+{
+    a.lq[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
+    a.lpre[i] = off;
+    const uint32_t w = (off + 31) >> 5;
+    if ((w << 5) < off + nq) a.wst[w] = i;
 }
 
 // What a slot does in the current step (the same in every CTA: each CTA's
@@ -218,38 +231,52 @@ struct SlotStep {
     uint32_t phase;
     uint32_t level;        // BFS level listed (kScan) or expanded (kExpand)
     uint32_t g0, G;        // the group: large-queue entries g0 .. g0 + G - 1
-    uint32_t nl, nch, nh;  // kExpand: small vertices, large-vertex chunks, large vertices
-    uint32_t nlong, nshort;  // work items: long ones first, then one-window chunks
+    uint32_t nl, nlq;      // kExpand: small vertices and their quads
+    uint32_t nch, nh;      // kExpand: large-vertex chunks, large vertices
+    uint32_t nlong, nshort;  // work items: windows of small quads (or scan / extraction items), large chunks
 };
 constexpr uint32_t kWordsPerItem = 8;     // bitmap words per extraction item
 constexpr uint32_t kScanPerItem = 256;    // vertices per scan item
 constexpr uint32_t kSlotOffset = 6;       // steps by which slot 1 starts after slot 0
 
 // Scan of vertices [v0, v0 + kScanPerItem): every vertex with new bits F has
-// them merged into vis, cleared from fn and is listed for expansion.
+// them merged into vis and cleared from fn, and is listed for expansion
+// unless it has no in-edges.
 __device__ __forceinline__ void scan_item(const DevGraph& g, const SlotArrays& a, uint32_t par, uint32_t v0,
                                           uint32_t lane)
 {
-    const uint32_t ltm = lanemask_lt_g();
     for (uint32_t r = 0; r < kScanPerItem; r += 32) {
         const uint32_t v = v0 + r + lane;
         const unsigned long long F = v < g.n ? __ldcg(a.fn + v) : 0ull;
         if (!__any_sync(kFull, F != 0ull)) continue;
-        bool small = false;
-        uint32_t rs = 0, re = 0;
+        uint32_t rs = 0, re = 0, nq = 0;
         if (F) {
             __stcg(a.fn + v, 0ull);
             __stcg(a.vis + v, __ldcg(a.vis + v) | F);
             range_of(g, v, rs, re);
-            small = list_large(a, par, rs, re, F);
+            nq = nquads(rs, re);
+            if (nq >= kGroupHeavyQ) {
+                list_large(a, par, rs, re, nq, F);
+                nq = 0;
+            }
         }
-        const uint32_t bal = __ballot_sync(kFull, small);
+        // small vertices of the warp: one packed reservation of entries and quads
+        uint32_t incl = nq;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, d);
+            if ((int)lane >= d) incl += t;
+        }
+        const uint32_t bal = __ballot_sync(kFull, nq != 0);
         if (bal) {
-            const int leader = __ffs(bal) - 1;
-            uint32_t base = 0;
-            if ((int)lane == leader) base = atomicAdd(&a.ct->lcount[par], (uint32_t)__popc(bal));
-            base = __shfl_sync(kFull, base, leader);
-            if (small) a.lq[base + __popc(bal & ltm)] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
+            unsigned long long base = 0;
+            if (lane == 31)
+                base = atomicAdd(&a.ct->lpack[par],
+                                 ((unsigned long long)__popc(bal) << kPackShift) | (unsigned long long)incl);
+            base = __shfl_sync(kFull, base, 31);
+            if (nq)
+                list_small(a, (uint32_t)(base >> kPackShift) + __popc(bal & lanemask_lt_g()),
+                           (uint32_t)(base & kPackLow) + incl - nq, rs, re, nq, F);
         }
     }
 }
@@ -279,46 +306,44 @@ __device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& 
     visit_quad(a.vis, a.fn, ql);
 }
 
-// 32 small vertices from lq[i0 ..): their quads flattened across lanes, in
-// windows of 32.  In a window, the run of each lane that meets it is
-// recorded at its first slot there; a slot's owner is the last recorded
-// start at or before it.
-__device__ __forceinline__ void small_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
-                                           const SlotArrays& a, uint32_t nl, uint32_t i0, uint4* rec,
-                                           unsigned long long* recF, uint32_t lane)
+// Window c of the level's small quads: quads [32c, 32c + 32) of the small
+// list, one per lane.  Its first entry is wst[c]; every entry has at least
+// one quad, so the window meets at most the 32 entries from there.  The run
+// of each entry that meets the window is recorded at its first slot there;
+// a slot's owner is the last recorded start at or before it.
+__device__ __forceinline__ void window_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
+                                            const SlotArrays& a, uint32_t nl, uint32_t nlq, uint32_t c,
+                                            uint4* rec, unsigned long long* recF, uint32_t lane)
 {
-    const uint32_t nf = min(nl - i0, 32u);
+    const uint32_t w0 = c << 5;
+    const uint32_t i = __ldcg(a.wst + c) + lane;
     uint4 e = make_uint4(0, 0, 0, 0);
-    if (lane < nf) e = __ldcg(a.lq + i0 + lane);
-    const uint32_t nq = nquads(e.x, e.y);
-    uint32_t incl = nq;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, d);
-        if ((int)lane >= d) incl += t;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    const uint32_t excl = incl - nq;
-    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-        const bool meets = nq != 0 && excl < j0 + 32 && incl > j0;
-        const uint32_t st = excl > j0 ? excl - j0 : 0u;
-        if (meets) {
-            rec[st] = make_uint4(e.x, e.y, excl, 0u);
-            recF[st] = ((unsigned long long)e.w << 32) | e.z;
+    uint32_t off = 0, nq = 0;
+    if (i < nl) {
+        off = __ldcg(a.lpre + i);
+        if (off < w0 + 32) {
+            e = __ldcg(a.lq + i);
+            nq = nquads(e.x, e.y);
         }
-        const uint32_t starts = __reduce_or_sync(kFull, meets ? 1u << st : 0u);
-        __syncwarp();
-        const uint32_t j = j0 + lane;
-        QuadLive ql = {};
-        if (j < total) {
-            const uint32_t pos = 31 - __clz(starts & lanemask_le_g());
-            const uint4 r = rec[pos];
-            const uint32_t quad = (r.x >> 2) + (j - r.z);
-            sweep_quad(g, rk, ps, quad, r.x, r.y, recF[pos], ql);
-        }
-        visit_quad(a.vis, a.fn, ql);
-        __syncwarp();
     }
+    const bool meets = nq != 0 && off + nq > w0;
+    const uint32_t st = off > w0 ? off - w0 : 0u;
+    if (meets) {
+        rec[st] = make_uint4(e.x, e.y, off, 0u);
+        recF[st] = ((unsigned long long)e.w << 32) | e.z;
+    }
+    const uint32_t starts = __reduce_or_sync(kFull, meets ? 1u << st : 0u);
+    __syncwarp();
+    const uint32_t j = w0 + lane;
+    QuadLive ql = {};
+    if (j < nlq) {
+        const uint32_t pos = 31 - __clz(starts & lanemask_le_g());
+        const uint4 r = rec[pos];
+        const uint32_t quad = (r.x >> 2) + (j - r.z);
+        sweep_quad(g, rk, ps, quad, r.x, r.y, recF[pos], ql);
+    }
+    visit_quad(a.vis, a.fn, ql);
+    __syncwarp();
 }
 
 // Count pass over words [w0, w0 + kWordsPerItem): members and in-edge sums
@@ -438,9 +463,11 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                 if (v.phase == kExpand) {
                     const uint32_t par = v.level & 1u;
                     const unsigned long long hp = __ldcg(&ct->hpack[par]);
-                    v.nh = (uint32_t)(hp >> 40);
-                    v.nch = (uint32_t)(hp & kLow40);
-                    v.nl = __ldcg(&ct->lcount[par]);
+                    const unsigned long long lp = __ldcg(&ct->lpack[par]);
+                    v.nh = (uint32_t)(hp >> kPackShift);
+                    v.nch = (uint32_t)(hp & kPackLow);
+                    v.nl = (uint32_t)(lp >> kPackShift);
+                    v.nlq = (uint32_t)(lp & kPackLow);
                     if (v.nch == 0 && v.nl == 0) v.phase = kCount;
                 }
                 if (v.phase == kIdle && s_next < large_count && (k == 0 || step >= kSlotOffset)) {
@@ -449,7 +476,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                     v.G = min(kGroupSets, large_count - s_next);
                     s_next += kGroupSets;
                 }
-                v.nlong = v.phase == kExpand ? (v.nl + 31) / 32
+                v.nlong = v.phase == kExpand ? (v.nlq + 31) / 32
                         : v.phase == kScan ? sitems
                         : (v.phase == kCount || v.phase == kWrite) ? witems : 0u;
                 v.nshort = v.phase == kExpand ? v.nch : 0u;
@@ -477,7 +504,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                     // level 0: the roots, listed directly
                     if (tid < 2) {
                         a.ct->hpack[tid] = 0;
-                        a.ct->lcount[tid] = 0;
+                        a.ct->lpack[tid] = 0;
                     }
                     if (tid < kGroupSets) {
                         a.ct->cnt[tid] = 0;
@@ -498,9 +525,14 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                         __stcg(a.vis + root, F);
                         uint32_t rs, re;
                         range_of(g, root, rs, re);
-                        if (list_large(a, 0, rs, re, F))
-                            a.lq[atomicAdd(&a.ct->lcount[0], 1u)] =
-                                make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
+                        const uint32_t nq = nquads(rs, re);
+                        if (nq >= kGroupHeavyQ) {
+                            list_large(a, 0, rs, re, nq, F);
+                        } else if (nq) {
+                            const unsigned long long old =
+                                atomicAdd(&a.ct->lpack[0], (1ull << kPackShift) | (unsigned long long)nq);
+                            list_small(a, (uint32_t)(old >> kPackShift), (uint32_t)(old & kPackLow), rs, re, nq, F);
+                        }
                     }
                 }
             } else if (v.phase == kExpand) {
@@ -509,7 +541,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                     // previous expansion step
                     const uint32_t np = (v.level + 1) & 1u;
                     a.ct->hpack[np] = 0;
-                    a.ct->lcount[np] = 0;
+                    a.ct->lpack[np] = 0;
                 }
                 if (v.nh <= kHeavySmem)
                     for (uint32_t i = tid; i < v.nh; i += kGroupThreads) s_hbase[k * kHeavySmem + i] = __ldcg(a.hb + i);
@@ -560,7 +592,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
             if (!lng) {
                 large_item(g, b.rk, s_ps[k], a, s_hbase + k * kHeavySmem, v.nh <= kHeavySmem, v.nh, ci, lane);
             } else if (v.phase == kExpand) {
-                small_item(g, b.rk, s_ps[k], a, v.nl, ci * 32, s_rec[wid], s_recF[wid], lane);
+                window_item(g, b.rk, s_ps[k], a, v.nl, v.nlq, ci, s_rec[wid], s_recF[wid], lane);
             } else if (v.phase == kScan) {
                 scan_item(g, a, v.level & 1u, ci * kScanPerItem, lane);
             } else if (v.phase == kCount) {
