@@ -411,15 +411,14 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     const uint64_t o_fn = up(n * 8), o_lq = o_fn + up(n * 8), o_lpre = o_lq + up(n * 16);
     const uint64_t o_wst = o_lpre + up(n * 4), o_hb = o_wst + up(wcap * 4);
     const uint64_t o_he = o_hb + up(hcap * 4), slot = o_he + up(hcap * 16);
-    const uint64_t o_ct = 2 * slot;
-    const uint64_t bytes = o_ct + up(2 * sizeof(GroupCounters));
+    const uint64_t o_ct = kGroupSlots * slot;
+    const uint64_t bytes = o_ct + up(kGroupSlots * sizeof(GroupCounters));
     char* p;
     if (c->grp.bytes < bytes) {
         TRY(dalloc(c, c->grp, bytes));
         p = static_cast<char*>(c->grp.p);
-        CK(cudaMemsetAsync(p, 0, o_lq, c->stream));
-        CK(cudaMemsetAsync(p + slot, 0, o_lq, c->stream));
-        CK(cudaMemsetAsync(p + o_ct, 0, 2 * sizeof(GroupCounters), c->stream));
+        for (uint32_t k = 0; k < kGroupSlots; ++k) CK(cudaMemsetAsync(p + k * slot, 0, o_lq, c->stream));
+        CK(cudaMemsetAsync(p + o_ct, 0, kGroupSlots * sizeof(GroupCounters), c->stream));
     }
     p = static_cast<char*>(c->grp.p);
     gs->vis = reinterpret_cast<unsigned long long*>(p);

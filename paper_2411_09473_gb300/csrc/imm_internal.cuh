@@ -249,9 +249,10 @@ cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const Devic
 cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
                            const DeviceInfo& di, cudaStream_t st);
 // Grouped IC large path: the large sets of a batch, 64 at a time, as one
-// multi-source BFS over the whole GPU (cooperative launch), two groups in
-// flight (two slots of the arrays below).
+// multi-source BFS over the whole GPU (cooperative launch), kGroupSlots
+// groups in flight (slots of the arrays below).
 constexpr uint32_t kGroupSets = 64;
+constexpr uint32_t kGroupSlots = 4;  // groups in flight
 struct GroupCounters {
     unsigned long long hpack[2];      // listed large vertices << 36 | their chunks, by level parity
     unsigned long long lpack[2];      // listed small vertices << 36 | their quads, by level parity
@@ -270,8 +271,8 @@ struct GroupScratch {
     uint32_t* wst;            // [wcap] first small entry of each 32-quad window
     uint32_t* hb;             // [hcap] first chunk of each large vertex of the level
     uint4* he;                // [hcap] large vertices: (rs, re, F lo, F hi)
-    uint64_t stride;          // bytes from each slot-0 array to its slot-1 twin
-    GroupCounters* ctr;       // [2], one per slot (ctr[0].claim serves both)
+    uint64_t stride;          // bytes from each slot's arrays to the next slot's
+    GroupCounters* ctr;       // [kGroupSlots], one per slot (ctr[0].claim serves all)
 };
 int ic_group_supported(const DeviceInfo& di);
 uint64_t ic_group_heavy_cap(uint32_t n, uint64_t m);

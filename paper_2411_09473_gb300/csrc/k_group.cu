@@ -35,11 +35,12 @@
 // size and in-edge sum, reserve its output (member list, or an n-bit bitmap
 // when the list would be larger; Sec. IV-C), write it, and clear vis.
 //
-// Two groups are in flight, in two slots of the arrays, the second started a
-// few steps after the first: every step serves both (long items of both
-// first, then the one-window chunks, which even out the end of the step), so
-// one group's small levels, scans and extraction passes overlap the other
-// group's big levels.
+// kGroupSlots groups are in flight, in slots of the arrays, each started a
+// few steps after the previous one: every step serves all of them (long
+// items first, then the one-window chunks, which even out the end of the
+// step), so the fixed cost of a step (its last item and the grid barrier) is
+// shared by several groups, and one group's small levels, scans and
+// extraction passes overlap the others' big levels.
 #include "imm_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -58,7 +59,7 @@ constexpr uint32_t kGroupHeavyQ = 32;  // in-edge quads from which a vertex is s
 // packed list counters: entries << 36 | quads (small list) or chunks (large list)
 constexpr int kPackShift = 36;
 constexpr unsigned long long kPackLow = (1ull << kPackShift) - 1;
-constexpr uint32_t kHeavySmem = 6144;  // chunk prefix entries per slot searched in shared memory
+constexpr uint32_t kHeavySmem = 10240;  // chunk prefix entries per slot searched in shared memory
 
 __device__ __forceinline__ uint32_t lanemask_le_g()
 {
@@ -175,7 +176,7 @@ __device__ __forceinline__ void visit_quad(const unsigned long long* vis, unsign
     }
 }
 
-// Arrays of one group slot (slot 1's lie `stride` bytes after slot 0's).
+// Arrays of one group slot (slot k's lie k * `stride` bytes after slot 0's).
 struct SlotArrays {
     unsigned long long *vis, *fn;
     uint4 *lq, *he;
@@ -185,7 +186,7 @@ struct SlotArrays {
 
 __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32_t k)
 {
-    const uint64_t d = k ? gs.stride : 0;
+    const uint64_t d = (uint64_t)k * gs.stride;
     auto at = [d](auto* p) { return reinterpret_cast<decltype(p)>(reinterpret_cast<char*>(p) + d); };
     SlotArrays a;
     a.vis = at(gs.vis);
@@ -237,7 +238,7 @@ struct SlotStep {
 };
 constexpr uint32_t kWordsPerItem = 8;     // bitmap words per extraction item
 constexpr uint32_t kScanPerItem = 256;    // vertices per scan item
-constexpr uint32_t kSlotOffset = 6;       // steps by which slot 1 starts after slot 0
+constexpr uint32_t kSlotOffset = 4;       // steps by which slot k starts after slot k - 1
 
 // Scan of vertices [v0, v0 + kScanPerItem): every vertex with new bits F has
 // them merged into vis and cleared from fn, and is listed for expansion
@@ -415,13 +416,15 @@ __device__ __forceinline__ void write_item(const DevGraph& g, const SampleBatch&
 __global__ void __launch_bounds__(kGroupThreads, kGroupBlocks)
 ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
 {
-    extern __shared__ uint32_t s_hbase[];  // [2][kHeavySmem] copies of the levels' chunk prefixes
-    __shared__ PhiloxSet s_ps[2][kGroupSets];
+    extern __shared__ uint32_t s_hbase[];  // [kGroupSlots][kHeavySmem] copies of the levels' chunk prefixes
+    __shared__ PhiloxSet s_ps[kGroupSlots][kGroupSets];
     __shared__ uint4 s_rec[kGroupWarps][32];                // run records: rs, re, first slot
     __shared__ unsigned long long s_recF[kGroupWarps][32];  // run records: new bits
-    __shared__ uint32_t s_cnt[2][kGroupSets], s_edg[2][kGroupSets], s_kind[2][kGroupSets];
-    __shared__ unsigned long long s_pos[2][kGroupSets];
-    __shared__ SlotStep s_st[2];
+    __shared__ uint32_t s_cnt[kGroupSlots][kGroupSets], s_edg[kGroupSlots][kGroupSets];
+    __shared__ uint32_t s_kind[kGroupSlots][kGroupSets];
+    __shared__ unsigned long long s_pos[kGroupSlots][kGroupSets];
+    __shared__ SlotStep s_st[kGroupSlots];
+    __shared__ uint32_t s_lbase[kGroupSlots + 1], s_sbase[kGroupSlots + 1];  // item ranges of the step
     __shared__ uint32_t s_next;
 
     cg::grid_group grid = cg::this_grid();
@@ -434,14 +437,13 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
     uint32_t* claim = gs.ctr[0].claim;
 
     if (tid == 0) {
-        s_st[0].phase = kIdle;
-        s_st[1].phase = kIdle;
+        for (uint32_t k = 0; k < kGroupSlots; ++k) s_st[k].phase = kIdle;
         s_next = 0;
     }
     for (uint32_t step = 0;; ++step) {
-        // ---- advance both slots (thread 0 of every CTA, same inputs)
+        // ---- advance every slot (thread 0 of every CTA, same inputs)
         if (tid == 0) {
-            for (uint32_t k = 0; k < 2; ++k) {
+            for (uint32_t k = 0; k < kGroupSlots; ++k) {
                 SlotStep& v = s_st[k];
                 const GroupCounters* ct = gs.ctr + k;
                 const uint32_t was = v.phase;
@@ -470,7 +472,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                     v.nlq = (uint32_t)(lp & kPackLow);
                     if (v.nch == 0 && v.nl == 0) v.phase = kCount;
                 }
-                if (v.phase == kIdle && s_next < large_count && (k == 0 || step >= kSlotOffset)) {
+                if (v.phase == kIdle && s_next < large_count && step >= k * kSlotOffset) {
                     v.phase = kInit;
                     v.g0 = s_next;
                     v.G = min(kGroupSets, large_count - s_next);
@@ -481,9 +483,23 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                         : (v.phase == kCount || v.phase == kWrite) ? witems : 0u;
                 v.nshort = v.phase == kExpand ? v.nch : 0u;
             }
+            // item ranges: the long items of all slots, then the one-window chunks
+            uint32_t x = 0;
+            for (uint32_t k = 0; k < kGroupSlots; ++k) {
+                s_lbase[k] = x;
+                x += s_st[k].nlong;
+            }
+            s_lbase[kGroupSlots] = x;
+            for (uint32_t k = 0; k < kGroupSlots; ++k) {
+                s_sbase[k] = x;
+                x += s_st[k].nshort;
+            }
+            s_sbase[kGroupSlots] = x;
         }
         __syncthreads();
-        if (s_st[0].phase == kIdle && s_st[1].phase == kIdle && s_next >= large_count) {
+        bool idle = s_next >= large_count;
+        for (uint32_t k = 0; k < kGroupSlots; ++k) idle = idle && s_st[k].phase == kIdle;
+        if (idle) {
             // every CTA is past the last barrier: leave the claim counters
             // zero for the next launch
             if (blockIdx.x == 0 && tid < 3) claim[tid] = 0;
@@ -492,7 +508,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
 
         // ---- per-CTA preparation of each slot's step
         if (blockIdx.x == 0 && tid == 0) claim[(step + 2) % 3] = 0;  // the step before this one's
-        for (uint32_t k = 0; k < 2; ++k) {
+        for (uint32_t k = 0; k < kGroupSlots; ++k) {
             const SlotStep v = s_st[k];
             const SlotArrays a = slot_arrays(gs, k);
             if (v.phase == kInit) {
@@ -570,10 +586,9 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
         }
         __syncthreads();
 
-        // ---- work items of both slots from one counter: the long items of
-        // both slots first, then the one-window chunks (they even out the end)
-        const uint32_t l0 = s_st[0].nlong, l1 = s_st[1].nlong, h0 = s_st[0].nshort;
-        const uint32_t total = l0 + l1 + h0 + s_st[1].nshort;
+        // ---- work items of all slots from one counter: the long items of
+        // every slot first, then the one-window chunks (they even out the end)
+        const uint32_t total = s_sbase[kGroupSlots];
         uint32_t* cl = claim + step % 3;
         uint32_t c = 0;
         if (lane == 0) c = atomicAdd(cl, 1u);
@@ -581,12 +596,11 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
         while (c < total) {
             uint32_t cn = 0;  // the next claim, in flight while this item runs
             if (lane == 0) cn = atomicAdd(cl, 1u);
-            uint32_t k, ci;
-            bool lng;
-            if (c < l0) { k = 0; ci = c; lng = true; }
-            else if (c < l0 + l1) { k = 1; ci = c - l0; lng = true; }
-            else if (c < l0 + l1 + h0) { k = 0; ci = c - l0 - l1; lng = false; }
-            else { k = 1; ci = c - l0 - l1 - h0; lng = false; }
+            const bool lng = c < s_lbase[kGroupSlots];
+            const uint32_t* base = lng ? s_lbase : s_sbase;
+            uint32_t k = 0;
+            while (c >= base[k + 1]) ++k;
+            const uint32_t ci = c - base[k];
             const SlotStep& v = s_st[k];
             const SlotArrays a = slot_arrays(gs, k);
             if (!lng) {
@@ -603,7 +617,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
             c = __shfl_sync(kFull, cn, 0);
         }
         __syncthreads();
-        for (uint32_t k = 0; k < 2; ++k) {
+        for (uint32_t k = 0; k < kGroupSlots; ++k) {
             if (s_st[k].phase == kCount && tid < s_st[k].G) {
                 GroupCounters* ct = gs.ctr + k;
                 atomicAdd(&ct->cnt[tid], s_cnt[k][tid]);
@@ -614,7 +628,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
     }
 }
 
-constexpr size_t kGroupDynSmem = 2 * kHeavySmem * 4;
+constexpr size_t kGroupDynSmem = (size_t)kGroupSlots * kHeavySmem * 4;
 
 int ic_group_supported(const DeviceInfo& di)
 {
