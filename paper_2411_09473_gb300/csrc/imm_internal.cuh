@@ -252,7 +252,7 @@ cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeS
 // multi-source BFS over the whole GPU (cooperative launch), kGroupSlots
 // groups in flight (slots of the arrays below).
 constexpr uint32_t kGroupSets = 64;
-constexpr uint32_t kGroupSlots = 4;  // groups in flight
+constexpr uint32_t kGroupSlots = 8;  // groups in flight
 struct GroupCounters {
     unsigned long long hpack[2];      // listed large vertices << 36 | their chunks, by level parity
     unsigned long long lpack[2];      // listed small vertices << 36 | their quads, by level parity

@@ -59,7 +59,7 @@ constexpr uint32_t kGroupHeavyQ = 32;  // in-edge quads from which a vertex is s
 // packed list counters: entries << 36 | quads (small list) or chunks (large list)
 constexpr int kPackShift = 36;
 constexpr unsigned long long kPackLow = (1ull << kPackShift) - 1;
-constexpr uint32_t kHeavySmem = 10240;  // chunk prefix entries per slot searched in shared memory
+constexpr uint32_t kHeavySmem = 4096;  // chunk prefix entries per slot searched in shared memory
 
 __device__ __forceinline__ uint32_t lanemask_le_g()
 {
@@ -238,7 +238,7 @@ struct SlotStep {
 };
 constexpr uint32_t kWordsPerItem = 8;     // bitmap words per extraction item
 constexpr uint32_t kScanPerItem = 256;    // vertices per scan item
-constexpr uint32_t kSlotOffset = 4;       // steps by which slot k starts after slot k - 1
+constexpr uint32_t kSlotOffset = 2;       // steps by which slot k starts after slot k - 1
 
 // Scan of vertices [v0, v0 + kScanPerItem): every vertex with new bits F has
 // them merged into vis and cleared from fn, and is listed for expansion
