@@ -24,6 +24,9 @@ Parity status per function (what pins it, tests/test_oracle_*.py):
                       martingale tail bound it solves; ell' vs n^-ell / 2^ell
   run                 composition of the above; stopping rule checked
                       against theta_params on every round
+  run (fresh_final)   same ladder as the plain run; final stream is exactly
+                      theta sets equal to an independent sample under the
+                      second key; RIS identity of its covered fraction
 """
 from __future__ import annotations
 
@@ -39,6 +42,7 @@ _LIB = os.path.join(_HERE, "_oracle.so")
 _lib = None
 
 OK, EINVAL, ENOMEM = 0, 1, 2
+FRESH_KEY = 0x9E3779B97F4A7C15  # key of the fresh final stream: seed ^ FRESH_KEY
 IC, LT = 0, 1
 
 
@@ -88,6 +92,7 @@ def _load():
         "orc_select_sets": ([u32, u64, vp, vp, u32, vp, ctypes.POINTER(u64)], i32),
         "orc_select": ([vp, u32, vp, ctypes.POINTER(u64)], i32),
         "orc_run": ([vp, u32, f64, f64, u64, vp, ctypes.POINTER(Stats)], i32),
+        "orc_run_ex": ([vp, u32, f64, f64, u64, u32, vp, ctypes.POINTER(Stats)], i32),
         "orc_num_sets": ([vp], u64),
         "orc_num_members": ([vp], u64),
         "orc_get_set": ([vp, u64, vp, u32, ctypes.POINTER(u32)], i32),
@@ -196,10 +201,13 @@ class Oracle:
             raise ValueError(f"orc_select -> {rc}")
         return seeds, int(cov.value)
 
-    def run(self, k: int, eps: float, ell: float, seed: int):
+    def run(self, k: int, eps: float, ell: float, seed: int, fresh_final: bool = False):
+        """Alg. 1; fresh_final: the final selection uses a fresh stream of
+        exactly theta sets drawn under seed ^ FRESH_KEY (Chen 2018's
+        correction of the set reuse)."""
         seeds = np.zeros(k, dtype=np.uint32)
         st = Stats()
-        rc = _load().orc_run(self._h, k, eps, ell, seed, _p(seeds), ctypes.byref(st))
+        rc = _load().orc_run_ex(self._h, k, eps, ell, seed, 1 if fresh_final else 0, _p(seeds), ctypes.byref(st))
         if rc != OK:
             raise ValueError(f"orc_run -> {rc}")
         return seeds, st

@@ -394,9 +394,18 @@ int orc_select(orc_ctx* c, uint32_t k, uint32_t* seeds, uint64_t* covered)
     return orc_select_sets(c->n, c->nsets, c->off, c->mem, k, seeds, covered);
 }
 
-/* Alg. 1 with Tang et al.'s Theta_Estimation / OPT_Lower_Bound / Set_Theta. */
-int orc_run(orc_ctx* c, uint32_t k, double eps, double ell, uint64_t seed,
-            uint32_t* seeds, orc_stats* st)
+/* Key of the fresh final stream (Chen 2018): the estimation phase's sets are
+ * dropped and theta new ones drawn under a second key, seed xor this odd
+ * constant (2^64 / golden ratio), so they are independent of the sets that
+ * fixed theta.  The paper reuses the sets (Alg. 1); the constant is a reading. */
+#define ORC_FRESH_KEY 0x9E3779B97F4A7C15ull
+#define ORC_FRESH_FINAL 1u
+
+/* Alg. 1 with Tang et al.'s Theta_Estimation / OPT_Lower_Bound / Set_Theta;
+ * flags & ORC_FRESH_FINAL: the final selection runs on a fresh stream of
+ * exactly theta sets. */
+int orc_run_ex(orc_ctx* c, uint32_t k, double eps, double ell, uint64_t seed, uint32_t flags,
+               uint32_t* seeds, orc_stats* st)
 {
     if (k == 0 || k > c->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0)) return ORC_EINVAL;
     orc_reset(c);
@@ -435,13 +444,23 @@ int orc_run(orc_ctx* c, uint32_t k, double eps, double ell, uint64_t seed,
     const uint64_t theta = (uint64_t)tf;
     st->lb = lb;
     st->theta = theta;
-    const uint64_t target = theta > c->nsets ? theta : c->nsets;
+    uint64_t target = theta > c->nsets ? theta : c->nsets;
+    if (flags & ORC_FRESH_FINAL) {
+        orc_reset(c);
+        seed ^= ORC_FRESH_KEY;
+        target = theta;
+    }
     if ((rc = orc_sample(c, target, seed)) != ORC_OK) return rc;
     uint64_t cov = 0;
     if ((rc = orc_select(c, k, seeds, &cov)) != ORC_OK) return rc;
     st->num_sets = c->nsets;
     st->covered = cov;
     return ORC_OK;
+}
+
+int orc_run(orc_ctx* c, uint32_t k, double eps, double ell, uint64_t seed, uint32_t* seeds, orc_stats* st)
+{
+    return orc_run_ex(c, k, eps, ell, seed, 0u, seeds, st);
 }
 
 /* ---- accessors for tests ---- */

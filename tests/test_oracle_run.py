@@ -67,3 +67,36 @@ def test_run_is_deterministic():
     s1, st1 = a.run(5, 0.4, 1.0, 99)
     s2, st2 = a.run(5, 0.4, 1.0, 99)
     assert np.array_equal(s1, s2) and st1.theta == st2.theta and st1.covered == st2.covered
+
+
+def test_fresh_final_stream():
+    # Chen 2018's correction: the estimation ladder is unchanged, and the final
+    # selection runs on exactly theta fresh sets, which are the sets an
+    # independent sampler draws under the second key.  Catches a missing reset
+    # (stream longer than theta or reusing old sets), a wrong key, and any
+    # change to the estimation phase.
+    for model, seed in ((graphgen.IC, 11), (graphgen.LT, 12)):
+        g = graphgen.make_graph(1500, 12000, seed, model, "inv_indeg")
+        k, eps, ell = 6, 0.5, 1.0
+        plain = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+        s0, st0 = plain.run(k, eps, ell, seed)
+        fresh = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+        s1, st1 = fresh.run(k, eps, ell, seed, fresh_final=True)
+        for f in ("rounds", "stopped_early", "lb", "theta", "lambda_prime", "lambda_star"):
+            assert getattr(st1, f) == getattr(st0, f), f
+        for i in range(st0.rounds):
+            assert st1.theta_i[i] == st0.theta_i[i]
+            assert st1.covered_i[i] == st0.covered_i[i]
+            assert st1.sets_i[i] == st0.sets_i[i]
+        assert st1.num_sets == st1.theta and fresh.num_sets == st1.theta
+        indep = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+        indep.sample(st1.theta, seed ^ oracle.FRESH_KEY)
+        off1, mem1 = fresh.arena()
+        off2, mem2 = indep.arena()
+        assert np.array_equal(off1, off2) and np.array_equal(mem1, mem2)
+        s2, c2 = oracle.select_sets(g.n, off2, mem2, k)
+        assert np.array_equal(s1, s2) and st1.covered == c2
+        # the fresh stream shares no set with the estimation stream's prefix
+        off0, mem0 = plain.arena()
+        same = sum(np.array_equal(mem0[off0[i]:off0[i + 1]], mem1[off1[i]:off1[i + 1]]) for i in range(200))
+        assert same < 200
