@@ -160,6 +160,21 @@ int imm_select(imm_ctx* ctx, uint32_t k, uint32_t* seeds_out, uint64_t* covered_
 int imm_run(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell,
             uint64_t rng_seed, uint32_t* seeds_out, imm_stats* stats_out);
 
+/* imm_run with options (flags: OR of IMM_RUN_*).
+ * IMM_RUN_FRESH_FINAL: the final selection runs on a fresh stream.  Once the
+ * estimation rounds have fixed LB and theta, their sets are dropped, and
+ * exactly theta new sets are sampled under the key rng_seed ^
+ * IMM_FRESH_FINAL_KEY.  They are independent of the sets that fixed theta.
+ * This is Chen's 2018 correction of Alg. 1's reuse of those sets; the paper
+ * reuses them.  The estimation rounds, LB and theta are the same as
+ * imm_run's.  stats_out->num_sets is theta, and the stream left in the
+ * context is the fresh one.
+ * flags == 0 is imm_run.  Errors: as imm_run, and EINVAL for unknown flags. */
+#define IMM_RUN_FRESH_FINAL 1u
+#define IMM_FRESH_FINAL_KEY 0x9E3779B97F4A7C15ull
+int imm_run_ex(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell,
+               uint64_t rng_seed, uint32_t flags, uint32_t* seeds_out, imm_stats* stats_out);
+
 /* One query of a batch: the context holding its graph (loaded with
  * imm_load_graph; the model is the graph's), and IMM's parameters. */
 typedef struct imm_query {

@@ -433,11 +433,13 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     return IMM_OK;
 }
 
-// The grouped path pays two dense passes over n per group of 64 sets and a
-// grid barrier per BFS level, so it is taken when there are enough large sets and
-// they are big (judged from the previous batches); it launches cooperatively,
-// so contexts whose streams run beside others' (batch and server workers)
-// keep the one-set-per-CTA path.
+// The grouped path pays dense passes over n and grid barriers per BFS level
+// for every group of 64 sets; it wins when the sets are giant and share the
+// graph's core (thousands of members and more).  So it is taken when there
+// are enough large sets and their mean size, from the previous batches, is at
+// least max(4096, n/64); before any batch has told, on graphs of >= 2^19
+// vertices only.  It launches cooperatively, so contexts whose streams run
+// beside others' (batch and server workers) keep the one-set-per-CTA path.
 // IMM_IC_LARGE=cta|group overrides the choice (both give the same sets).
 bool use_group(const imm_ctx* c, uint32_t large_count)
 {
@@ -447,7 +449,8 @@ bool use_group(const imm_ctx* c, uint32_t large_count)
     if (!ic_group_supported(c->di)) return false;
     if (force && strcmp(force, "group") == 0) return true;
     if (large_count < kGroupSets) return false;
-    return c->large_mean <= 0.0 || c->large_mean * kGroupSets >= (double)c->n / 4.0;
+    if (c->large_mean > 0.0) return c->large_mean >= std::max(4096.0, (double)c->n / 64.0);
+    return c->n >= (1u << 19);
 }
 
 int index_limit_ok(imm_ctx* c, uint64_t more_bytes)
@@ -1329,7 +1332,14 @@ int imm_set_arena_limit(imm_ctx* c, uint64_t bytes)
 int imm_run(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint64_t rng_seed, uint32_t* seeds_out,
             imm_stats* stats_out)
 {
+    return imm_run_ex(c, model, k, epsilon, ell, rng_seed, 0u, seeds_out, stats_out);
+}
+
+int imm_run_ex(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint64_t rng_seed, uint32_t flags,
+               uint32_t* seeds_out, imm_stats* stats_out)
+{
     if (!c) return IMM_EINVAL;
+    if (flags & ~IMM_RUN_FRESH_FINAL) return set_err(c, IMM_EINVAL, "unknown flags 0x%x", flags);
     DeviceGuard guard(c->device);
     const auto t0 = std::chrono::steady_clock::now();
     if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
@@ -1376,7 +1386,12 @@ int imm_run(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint6
     const uint64_t theta = (uint64_t)tf;
     st.lb = lb;
     st.theta = theta;
-    TRY(sample_to(c, std::max<uint64_t>(theta, c->nsets), rng_seed));
+    if (flags & IMM_RUN_FRESH_FINAL) {
+        drop_stream(c);
+        TRY(sample_to(c, theta, rng_seed ^ IMM_FRESH_FINAL_KEY));
+    } else {
+        TRY(sample_to(c, std::max<uint64_t>(theta, c->nsets), rng_seed));
+    }
     uint64_t cov = 0;
     TRY(select_k(c, k, seeds_out, &cov));
     st.num_sets = c->nsets;

@@ -294,8 +294,10 @@ struct BlockTeam {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// s_red: one slot per warp of the block; the block's best key goes to the
+// round's key with one atomic (not one per warp: they all hit one address).
 template <class Team>
-__device__ void team_argmax(const SelectState& s, uint32_t j, Team t)
+__device__ void team_argmax(const SelectState& s, uint32_t j, Team t, unsigned long long* s_red)
 {
     // four vertices per step with 16-byte count loads (work is 256-byte
     // aligned); the ragged tail one by one
@@ -327,7 +329,18 @@ __device__ void team_argmax(const SelectState& s, uint32_t j, Team t)
         const unsigned long long o = __shfl_xor_sync(kFull, best, d);
         best = o > best ? o : best;
     }
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(&s.keys[j], best);
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 0) s_red[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+        best = lane < nwarps ? s_red[lane] : 0ull;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+            best = o > best ? o : best;
+        }
+        if (lane == 0 && best) atomicMax(&s.keys[j], best);
+    }
 }
 
 template <class Team>
@@ -470,10 +483,10 @@ __device__ void team_count_uncovered(const SelectState& s, uint32_t j, Team t)
 }
 
 template <class Team>
-__device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_mode)
+__device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_mode, unsigned long long* s_red)
 {
     for (uint32_t j = 0; j < k; ++j) {
-        team_argmax(s, j, t);
+        team_argmax(s, j, t, s_red);
         t.sync();
         team_cover(s, j, t);
         t.sync();
@@ -496,15 +509,17 @@ __global__ void __launch_bounds__(512)
 select_coop_kernel(SelectState s, uint32_t k)
 {
     __shared__ int s_mode;
-    select_rounds(s, k, GridTeam{}, &s_mode);
+    __shared__ unsigned long long s_red[32];
+    select_rounds(s, k, GridTeam{}, &s_mode, s_red);
 }
 
 __global__ void __launch_bounds__(512, 1)
 select_cta_kernel(const SelectState* states, const uint32_t* ks, uint32_t count)
 {
     __shared__ int s_mode;
+    __shared__ unsigned long long s_red[32];
     for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
-        select_rounds(states[i], ks[i], BlockTeam{}, &s_mode);
+        select_rounds(states[i], ks[i], BlockTeam{}, &s_mode, s_red);
         __syncthreads();
     }
 }

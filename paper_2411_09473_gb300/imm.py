@@ -110,6 +110,7 @@ def _load():
         "imm_sample": ([vp, i32, u64, u64], i32),
         "imm_select": ([vp, u32, vp, ctypes.POINTER(u64)], i32),
         "imm_run": ([vp, i32, u32, f64, f64, u64, vp, ctypes.POINTER(imm_stats)], i32),
+        "imm_run_ex": ([vp, i32, u32, f64, f64, u64, u32, vp, ctypes.POINTER(imm_stats)], i32),
         "imm_reset_sets": ([vp], i32),
         "imm_stream_size": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
         "imm_get_set": ([vp, u64, vp, u32, ctypes.POINTER(u32)], i32),
@@ -239,6 +240,17 @@ def imm_run(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_seed:
     seeds = np.zeros(max(k, 1), dtype=np.uint32)
     st = imm_stats()
     _check(ctx, _load().imm_run(ctx.handle, model, k, epsilon, ell, rng_seed, seeds.ctypes.data, ctypes.byref(st)))
+    return seeds[:k], st
+
+
+IMM_RUN_FRESH_FINAL = 1
+
+
+def imm_run_ex(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_seed: int, flags: int):
+    seeds = np.zeros(max(k, 1), dtype=np.uint32)
+    st = imm_stats()
+    _check(ctx, _load().imm_run_ex(ctx.handle, model, k, epsilon, ell, rng_seed, flags, seeds.ctypes.data,
+                                   ctypes.byref(st)))
     return seeds[:k], st
 
 

@@ -241,11 +241,14 @@ def test_select_k_equals_n_and_empty_stream(imm):
     assert np.array_equal(seeds, want) and cov == wcov == 500
 
 
-def check_run(imm, g, k, eps, ell, seed):
+def check_run(imm, g, k, eps, ell, seed, fresh_final=False):
     ctx = new_ctx(imm, g)
-    seeds, st = imm.imm_run(ctx, g.model, k, eps, ell, seed)
+    if fresh_final:
+        seeds, st = imm.imm_run_ex(ctx, g.model, k, eps, ell, seed, imm.IMM_RUN_FRESH_FINAL)
+    else:
+        seeds, st = imm.imm_run(ctx, g.model, k, eps, ell, seed)
     o = oracle_for(g)
-    want, ost = o.run(k, eps, ell, seed)
+    want, ost = o.run(k, eps, ell, seed, fresh_final=fresh_final)
     assert np.array_equal(seeds, want)
     assert st.rounds == ost.rounds and st.stopped_early == ost.stopped_early
     for i in range(st.rounds):
@@ -265,6 +268,17 @@ def check_run(imm, g, k, eps, ell, seed):
 def test_run_ic_weighted_cascade_4k(imm):
     w = graphgen.plain_workload("ic_wc_4k")
     check_run(imm, w.graph, w.k, w.epsilon, w.ell, w.seed)
+
+
+@pytest.mark.parametrize("model", [IC, LT])
+def test_run_fresh_final_stream(imm, model):
+    # the final selection on exactly theta fresh sets under the second key
+    g = graphgen.make_graph(3000, 30000, 17, model, "inv_indeg")
+    st = check_run(imm, g, 8, 0.4, 1.0, 17, fresh_final=True)
+    assert st.num_sets == st.theta
+    ctx = new_ctx(imm, g)
+    with pytest.raises(imm.ImmError):
+        imm.imm_run_ex(ctx, g.model, 8, 0.4, 1.0, 17, 2)
 
 
 def test_run_lt_small(imm):
