@@ -343,6 +343,20 @@ __device__ void team_argmax(const SelectState& s, uint32_t j, Team t, unsigned l
     }
 }
 
+// Appends the set ids of a warp's `take` lanes to the round's newly covered
+// list with one atomic per warp (the list's counter is a single address).
+__device__ __forceinline__ void append_newly(const SelectState& s, uint32_t j, bool take, uint32_t sid)
+{
+    const uint32_t bal = __ballot_sync(kFull, take);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&s.newly_n[j], (unsigned long long)__popc(bal));
+    base = __shfl_sync(kFull, base, leader);
+    if (take) s.newly[base + __popc(bal & ((1u << lane) - 1u))] = sid;
+}
+
 template <class Team>
 __device__ void team_cover(const SelectState& s, uint32_t j, Team t)
 {
@@ -352,18 +366,27 @@ __device__ void team_cover(const SelectState& s, uint32_t j, Team t)
         s.picked[v] = 1;
         s.seeds[j] = v;
     }
+    // warp-uniform loops (lane i of a warp takes element first + i), so the
+    // appends can be aggregated per warp
+    const uint64_t lane = threadIdx.x & 31;
+    const uint64_t wfirst = t.rank() - lane, tsize = t.size();
     unsigned long long vol = 0, nb = 0;
     for (uint32_t g = 0; g < s.nsegs; ++g) {
         const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
         const uint32_t* inv = s.segs[g].inv;
-        for (uint64_t i = a + t.rank(); i < b; i += t.size()) {
-            const uint32_t sid = inv[i];
-            if (!s.covered[sid]) {
-                s.covered[sid] = 1;
-                const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
-                s.newly[p] = sid;
-                vol += s.off[(uint64_t)sid + 1] - s.off[sid];
+        for (uint64_t i0 = a + wfirst; i0 < b; i0 += tsize) {
+            const uint64_t i = i0 + lane;
+            bool take = false;
+            uint32_t sid = 0;
+            if (i < b) {
+                sid = inv[i];
+                if (!s.covered[sid]) {
+                    s.covered[sid] = 1;
+                    take = true;
+                    vol += s.off[(uint64_t)sid + 1] - s.off[sid];
+                }
             }
+            append_newly(s, j, take, sid);
         }
     }
     if (vol) {
@@ -372,15 +395,20 @@ __device__ void team_cover(const SelectState& s, uint32_t j, Team t)
     }
     vol = 0;
     const uint32_t wv = v >> 5, bit = 1u << (v & 31);
-    for (uint64_t b = t.rank(); b < s.nbmp; b += t.size()) {
-        const uint32_t sid = s.bmp_set[b];
-        if (!s.covered[sid] && (s.bmp[b * s.words + wv] & bit)) {
-            s.covered[sid] = 1;
-            const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
-            s.newly[p] = sid;
-            vol += s.bmp_len[b];
-            ++nb;
+    for (uint64_t b0 = wfirst; b0 < s.nbmp; b0 += tsize) {
+        const uint64_t b = b0 + lane;
+        bool take = false;
+        uint32_t sid = 0;
+        if (b < s.nbmp) {
+            sid = s.bmp_set[b];
+            if (!s.covered[sid] && (s.bmp[b * s.words + wv] & bit)) {
+                s.covered[sid] = 1;
+                take = true;
+                vol += s.bmp_len[b];
+                ++nb;
+            }
         }
+        append_newly(s, j, take, sid);
     }
     if (vol) atomicAdd(&s.vol_cov[j], vol);
     if (nb) atomicAdd(&s.bmp_cov[j], nb);
@@ -443,11 +471,18 @@ __device__ void team_rebuild_add(const SelectState& s, Team t)
 template <class Team>
 __device__ void team_gather_uncovered(const SelectState& s, uint32_t j, Team t)
 {
-    for (uint64_t b = t.rank(); b < s.nbmp; b += t.size()) {
-        if (!s.covered[s.bmp_set[b]]) {
-            const unsigned long long p = atomicAdd(&s.ubmp_n[j], 1ull);
-            s.ubmp[p] = (uint32_t)b;
-        }
+    // warp-uniform loop with one append atomic per warp
+    const uint64_t lane = threadIdx.x & 31;
+    for (uint64_t b0 = t.rank() - lane; b0 < s.nbmp; b0 += t.size()) {
+        const uint64_t b = b0 + lane;
+        const bool take = b < s.nbmp && !s.covered[s.bmp_set[b]];
+        const uint32_t bal = __ballot_sync(kFull, take);
+        if (!bal) continue;
+        const int leader = __ffs(bal) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(&s.ubmp_n[j], (unsigned long long)__popc(bal));
+        base = __shfl_sync(kFull, base, leader);
+        if (take) s.ubmp[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)b;
     }
 }
 
