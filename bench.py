@@ -43,8 +43,8 @@ METRIC = "IMM seconds-to-seeds"
 # the GPU (SMs x 4 schedulers x 32 lanes x max SM clock).
 ALU_OPS_PER_QUAD_EVAL = 44
 # DRAM bytes per quad evaluation of the dominant IC kernel on the 1M-vertex
-# workload, from one ncu capture (profiles/ic_group_kernel__ic_u01_1m_first2000sets.md)
-IC_DRAM_BYTES_PER_QUAD_EVAL = 3.661495e9 / 1192743275
+# workload, from one ncu capture (profiles/ic_group_kernel__ic_u01_1m_first20000sets.md)
+IC_DRAM_BYTES_PER_QUAD_EVAL = 38.350062e9 / 12215037853
 WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "batch64", "served")
 
 

@@ -16,7 +16,7 @@
 //   scan    a dense pass over fn merges every nonzero fn[v] into vis[v],
 //           clears it and lists v with F = fn[v] for the next expansion:
 //           vertices with >= 32 in-edge quads in a large list with a running
-//           chunk count, the others in a small list.
+//           count of 64-quad chunks, the others in a small list.
 // vis changes only in scan steps, so expansions read it without races.  The
 // giant sets of a power-law graph walk the same high-degree core within a
 // level or two of each other, so the per-vertex work (edge range, threshold
@@ -27,9 +27,9 @@
 // and advances in steps separated by grid barriers; warps claim work items
 // from one counter.  Expansion items are 32-vertex chunks of the small list,
 // whose quads are flattened across lanes (one quad per lane, its owner found
-// from per-warp run records in shared memory; up to 31 windows of 32 quads
-// per item), and one-window 32-quad chunks of the large vertices (owner found
-// by a 32-way search over the chunk prefix).
+// from per-warp run records in shared memory), and 64-quad chunks of the
+// large vertices, two quads per lane sharing each set's bookkeeping (owner
+// found by a 32-way search over the chunk prefix).
 //
 // When no vertex is listed, two dense passes over vis give every set its
 // size and in-edge sum, reserve its output (member list, or an n-bit bitmap
@@ -37,7 +37,7 @@
 //
 // kGroupSlots groups are in flight, in slots of the arrays, each started a
 // few steps after the previous one: every step serves all of them (long
-// items first, then the one-window chunks, which even out the end of the
+// items first, then the large-vertex chunks, which even out the end of the
 // step), so the fixed cost of a step (its last item and the grid barrier) is
 // shared by several groups, and one group's small levels, scans and
 // extraction passes overlap the others' big levels.
@@ -55,7 +55,8 @@ constexpr int kGroupThreads = 1024;  // threads per CTA
 constexpr int kGroupBlocks = 1;      // CTAs per SM (the cooperative grid is SMs x this)
 constexpr int kGroupChains = 2;      // independent Philox chains per lane in a sweep
 constexpr int kGroupWarps = kGroupThreads / 32;
-constexpr uint32_t kGroupHeavyQ = 32;  // in-edge quads from which a vertex is swept in 32-quad chunks
+constexpr uint32_t kGroupHeavyQ = 32;  // in-edge quads from which a vertex is swept in chunks
+constexpr uint32_t kChunkQuads = 64;   // quads of a large vertex per work item (two per lane)
 // packed list counters: entries << 36 | quads (small list) or chunks (large list)
 constexpr int kPackShift = 36;
 constexpr unsigned long long kPackLow = (1ull << kPackShift) - 1;
@@ -155,6 +156,85 @@ __device__ __forceinline__ void sweep_quad(const DevGraph& g, const PhiloxKeys& 
     }
 }
 
+// One half (32 sets) for two quads of the same vertex (same sets): per set,
+// the two quads' Philox evaluations are the two independent chains, and the
+// set's bookkeeping is shared by both.
+__device__ __forceinline__ void sweep_half2(uint32_t mask, uint64_t aa, uint64_t ab, uint4 ta, uint4 tb,
+                                            const PhiloxSet* ps, const PhiloxKeys& rk, uint32_t* acc_a,
+                                            uint32_t* acc_b)
+{
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    while (mask) {
+        const int s = 31 - __clz(mask);
+        const uint32_t bit = 1u << s;
+        mask ^= bit;
+        const PhiloxSet p = ps[s];
+        const uint4 wa = philox_xa(aa, p, rk);
+        const uint4 wb = philox_xa(ab, p, rk);
+        if (wa.x <= ta.x) a0 |= bit;
+        if (wa.y <= ta.y) a1 |= bit;
+        if (wa.z <= ta.z) a2 |= bit;
+        if (wa.w <= ta.w) a3 |= bit;
+        if (wb.x <= tb.x) b0 |= bit;
+        if (wb.y <= tb.y) b1 |= bit;
+        if (wb.z <= tb.z) b2 |= bit;
+        if (wb.w <= tb.w) b3 |= bit;
+    }
+    acc_a[0] = a0;
+    acc_a[1] = a1;
+    acc_a[2] = a2;
+    acc_a[3] = a3;
+    acc_b[0] = b0;
+    acc_b[1] = b1;
+    acc_b[2] = b2;
+    acc_b[3] = b3;
+}
+
+// Thresholds of a quad as the compare bounds of sweep_half, and the mask of
+// its in-edges that are in [rs, re) and can be live (th > 0).
+__device__ __forceinline__ uint4 quad_bounds(const DevGraph& g, uint32_t quad, uint32_t rs, uint32_t re,
+                                             uint32_t* valid)
+{
+    const uint4 th = __ldg(reinterpret_cast<const uint4*>(g.thr) + quad);
+    uint32_t v = (th.x ? 1u : 0u) | (th.y ? 2u : 0u) | (th.z ? 4u : 0u) | (th.w ? 8u : 0u);
+    const uint32_t e0 = quad << 2;
+    if (e0 < rs) v &= 0xFu << (rs - e0);
+    if (e0 + 4 > re) v &= 0xFu >> (e0 + 4 - re);
+    *valid = v;
+    return make_uint4((th.x << 8) - 1u, (th.y << 8) - 1u, (th.z << 8) - 1u, (th.w << 8) - 1u);
+}
+
+__device__ __forceinline__ void mask_invalid(QuadLive& ql, uint32_t valid)
+{
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (!((valid >> t) & 1u)) {
+            ql.lo[t] = 0;
+            ql.hi[t] = 0;
+        }
+    }
+}
+
+// Coins of all sets in F for quads qa and qb = qa + 32 of one vertex (qb
+// beyond the vertex's last quad when !hb: its results are cleared).
+__device__ __forceinline__ void sweep_two(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
+                                          uint32_t qa, uint32_t qb, bool hb, uint32_t rs, uint32_t re,
+                                          unsigned long long F, QuadLive& la, QuadLive& lb)
+{
+    la.src = __ldg(reinterpret_cast<const uint4*>(g.src) + qa);
+    lb.src = hb ? __ldg(reinterpret_cast<const uint4*>(g.src) + qb) : make_uint4(0, 0, 0, 0);
+    uint32_t va, vb;
+    const uint4 ta = quad_bounds(g, qa, rs, re, &va);
+    uint4 tb = make_uint4(0, 0, 0, 0);
+    vb = 0;
+    if (hb) tb = quad_bounds(g, qb, rs, re, &vb);
+    const uint64_t aa = (uint64_t)kPhiloxM1 * (uint64_t)qa, ab = (uint64_t)kPhiloxM1 * (uint64_t)qb;
+    sweep_half2((uint32_t)F, aa, ab, ta, tb, ps, rk, la.lo, lb.lo);
+    sweep_half2((uint32_t)(F >> 32), aa, ab, ta, tb, ps + 32, rk, la.hi, lb.hi);
+    mask_invalid(la, va);
+    mask_invalid(lb, vb);
+}
+
 // Apply the live bits of one quad per lane: bits u has not been expanded for
 // are ored into fn[u] (no value returned: nothing waits on it).  The four
 // lookups of a lane are independent, so the visit costs one memory round
@@ -201,12 +281,12 @@ __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32
 }
 
 // A vertex with >= 32 in-edge quads and new bits F enters the level's large
-// list (32-quad chunks; chunk prefix in hb).
+// list (64-quad chunks; chunk prefix in hb).
 __device__ __forceinline__ void list_large(const SlotArrays& a, uint32_t par, uint32_t rs, uint32_t re,
                                            uint32_t nq, unsigned long long F)
 {
     const unsigned long long old =
-        atomicAdd(&a.ct->hpack[par], (1ull << kPackShift) | (unsigned long long)((nq + 31) >> 5));
+        atomicAdd(&a.ct->hpack[par], (1ull << kPackShift) | (unsigned long long)((nq + kChunkQuads - 1) / kChunkQuads));
     const uint32_t i = (uint32_t)(old >> kPackShift);
     a.hb[i] = (uint32_t)(old & kPackLow);
     a.he[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
@@ -282,9 +362,10 @@ __device__ __forceinline__ void scan_item(const DevGraph& g, const SlotArrays& a
     }
 }
 
-// 32-quad chunk hc of the level's large vertices.  Owner: the last lo with
-// hb[lo] <= hc (invariant hb[lo] <= hc < hb[lo + span]; lane 0 probes lo
-// itself, so the ballot is never empty).
+// 64-quad chunk hc of the level's large vertices: lane t sweeps quads t and
+// t + 32 of the chunk (the second only when some lane has one there).
+// Owner: the last lo with hb[lo] <= hc (invariant hb[lo] <= hc < hb[lo +
+// span]; lane 0 probes lo itself, so the ballot is never empty).
 __device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
                                            const SlotArrays& a, const uint32_t* s_hb, bool hsm, uint32_t nh,
                                            uint32_t hc, uint32_t lane)
@@ -300,11 +381,20 @@ __device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& 
     }
     const uint4 e = __ldcg(a.he + lo);
     const uint32_t first = hsm ? s_hb[lo] : __ldcg(a.hb + lo);
-    const uint32_t quad = (e.x >> 2) + (hc - first) * 32 + lane;
-    QuadLive ql = {};
-    if (quad <= ((e.y - 1) >> 2))
-        sweep_quad(g, rk, ps, quad, e.x, e.y, ((unsigned long long)e.w << 32) | e.z, ql);
-    visit_quad(a.vis, a.fn, ql);
+    const uint32_t qa = (e.x >> 2) + (hc - first) * kChunkQuads + lane, qb = qa + 32;
+    const uint32_t qlast = (e.y - 1) >> 2;
+    const unsigned long long F = ((unsigned long long)e.w << 32) | e.z;
+    const bool ha = qa <= qlast, hb = qb <= qlast;
+    QuadLive la = {};
+    if (__any_sync(kFull, hb)) {
+        QuadLive lb = {};
+        if (ha) sweep_two(g, rk, ps, qa, qb, hb, e.x, e.y, F, la, lb);
+        visit_quad(a.vis, a.fn, la);
+        visit_quad(a.vis, a.fn, lb);
+    } else {
+        if (ha) sweep_quad(g, rk, ps, qa, e.x, e.y, F, la);
+        visit_quad(a.vis, a.fn, la);
+    }
 }
 
 // Window c of the level's small quads: quads [32c, 32c + 32) of the small
@@ -483,7 +573,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                         : (v.phase == kCount || v.phase == kWrite) ? witems : 0u;
                 v.nshort = v.phase == kExpand ? v.nch : 0u;
             }
-            // item ranges: the long items of all slots, then the one-window chunks
+            // item ranges: the long items of all slots, then the large-vertex chunks
             uint32_t x = 0;
             for (uint32_t k = 0; k < kGroupSlots; ++k) {
                 s_lbase[k] = x;
@@ -587,7 +677,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
         __syncthreads();
 
         // ---- work items of all slots from one counter: the long items of
-        // every slot first, then the one-window chunks (they even out the end)
+        // every slot first, then the large-vertex chunks (they even out the end)
         const uint32_t total = s_sbase[kGroupSlots];
         uint32_t* cl = claim + step % 3;
         uint32_t c = 0;
