@@ -32,10 +32,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IMM seconds-to-seeds"
 
-# DRAM bytes per examined in-edge of ic_large_kernel, from one ncu capture of
-# the current kernel on the first 2,000 sets of the 1M-vertex IC workload
-# (profiles/ic_large_kernel__ic_u01_1m_first2000sets.md: 12.454 GB over
-# 4,620,412,076 in-edges).  Traffic of a full launch is scaled by its in-edges.
 # IC sampling is bound by integer issue, not by DRAM: its roofline counts coin
 # evaluations, one per (RRR set, in-edge quad) pair the BFS examines, each a
 # Philox4x32-10 draw (10 rounds of 2 wide 32x32 multiplies + 2 three-input
