@@ -414,6 +414,51 @@ __device__ void team_cover(const SelectState& s, uint32_t j, Team t)
     if (nb) atomicAdd(&s.bmp_cov[j], nb);
 }
 
+// Streams without bitmap-stored sets (small sets: decrementing is always the
+// cheaper update): cover and decrement in one pass, each warp removing the
+// members of the sets it has just covered, so a round needs one grid
+// barrier less.  Counts are identical to cover-then-decrement.
+template <class Team>
+__device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t)
+{
+    const unsigned long long key = s.keys[j];
+    const uint32_t v = 0xFFFFFFFFu - (uint32_t)key;
+    if (t.rank() == 0) {
+        s.picked[v] = 1;
+        s.seeds[j] = v;
+    }
+    const uint64_t lane = threadIdx.x & 31;
+    const uint64_t wfirst = t.rank() - lane, tsize = t.size();
+    unsigned long long vol = 0;
+    for (uint32_t g = 0; g < s.nsegs; ++g) {
+        const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
+        const uint32_t* inv = s.segs[g].inv;
+        for (uint64_t i0 = a + wfirst; i0 < b; i0 += tsize) {
+            const uint64_t i = i0 + lane;
+            uint64_t start = 0;
+            uint32_t len = 0;
+            bool take = false;
+            if (i < b) {
+                const uint32_t sid = inv[i];
+                if (!s.covered[sid]) {
+                    s.covered[sid] = 1;
+                    take = true;
+                    start = s.off[sid];
+                    len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                    vol += len;
+                }
+            }
+            const uint32_t bal = __ballot_sync(kFull, take);
+            if (lane == 0 && bal) atomicAdd(&s.newly_n[j], (unsigned long long)__popc(bal));
+            if (bal) warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);  // += -1
+        }
+    }
+    if (vol) {
+        atomicAdd(&s.vol_cov[j], vol);
+        atomicAdd(&s.vol_list[j], vol);
+    }
+}
+
 template <class Team>
 __device__ void team_decrement(const SelectState& s, uint32_t j, Team t)
 {
@@ -523,6 +568,11 @@ __device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_m
     for (uint32_t j = 0; j < k; ++j) {
         team_argmax(s, j, t, s_red);
         t.sync();
+        if (s.nbmp == 0) {
+            team_cover_decrement(s, j, t);
+            t.sync();
+            continue;
+        }
         team_cover(s, j, t);
         t.sync();
         if (threadIdx.x == 0) *s_mode = round_mode(s, j);
