@@ -608,6 +608,10 @@ int batch_phase2(imm_ctx* c)
         }
         b.big = P<uint32_t>(c->big);
         b.big_cap = c->big_cap;
+        // IMM_BIG_CAP_WORDS (tests): a smaller output buffer, at least one
+        // bitmap, drives the reservation-failure and resampling path
+        if (const char* cap = std::getenv("IMM_BIG_CAP_WORDS"))
+            b.big_cap = std::min<uint64_t>(b.big_cap, std::max<uint64_t>(std::strtoull(cap, nullptr, 10), words));
         const bool ic = c->model == IMM_IC;
         const DevGraph g = dev_graph(c);
         if (use_group(c, large_count)) {

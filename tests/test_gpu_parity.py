@@ -180,6 +180,19 @@ def test_ic_global_bitmap_path(imm, large_path):
         assert np.array_equal(got, want), s
 
 
+def test_ic_large_output_overflow_resamples(imm, large_path, monkeypatch):
+    # an output buffer of three bitmaps: most large sets fail their
+    # reservation and are resampled by later (smaller) batches; the stream
+    # must still be the oracle's, set for set
+    g = graphgen.make_graph(1 << 13, 1 << 16, 43, IC, "uniform", pmax=0.25)
+    words = (g.n + 31) // 32
+    monkeypatch.setenv("IMM_BIG_CAP_WORDS", str(3 * words))
+    ctx = new_ctx(imm, g)
+    check_stream(imm, ctx, g, 700, 43)
+    off, _ = imm.imm_get_sets(ctx, 0, 700)
+    assert (np.diff(off.astype(np.int64)) > 256).sum() > 50
+
+
 def test_ic_group_ragged_groups_lists_and_bitmaps(imm, monkeypatch):
     monkeypatch.setenv("IMM_IC_LARGE", "group")
     # R-MAT with giant sets over several batches: groups of 64 and ragged
