@@ -96,7 +96,9 @@ struct QuadLive {
 
 // One half (32 sets) of the mask: coins of every set in `mask` for the quad
 // whose round-0 product is `a`; with two chains, two sets per step so that
-// two independent Philox evaluations are in flight.
+// two independent Philox evaluations are in flight.  A set's bit enters each
+// accumulator at most once, so the live bits are added rather than ored
+// (the adds may issue on the multiply-add pipe, which the xors leave idle).
 __device__ __forceinline__ void sweep_half(uint32_t mask, uint64_t a, uint4 tm, const PhiloxSet* ps,
                                            const PhiloxKeys& rk, uint32_t* acc)
 {
@@ -112,15 +114,15 @@ __device__ __forceinline__ void sweep_half(uint32_t mask, uint64_t a, uint4 tm, 
             const uint32_t b2 = two ? 1u << s2 : 0u;
             mask ^= b2;
             const uint4 w2 = philox_xa(a, ps[s2], rk);
-            if (w2.x <= tm.x) a0 |= b2;
-            if (w2.y <= tm.y) a1 |= b2;
-            if (w2.z <= tm.z) a2 |= b2;
-            if (w2.w <= tm.w) a3 |= b2;
+            if (w2.x <= tm.x) a0 += b2;
+            if (w2.y <= tm.y) a1 += b2;
+            if (w2.z <= tm.z) a2 += b2;
+            if (w2.w <= tm.w) a3 += b2;
         }
-        if (w1.x <= tm.x) a0 |= b1;
-        if (w1.y <= tm.y) a1 |= b1;
-        if (w1.z <= tm.z) a2 |= b1;
-        if (w1.w <= tm.w) a3 |= b1;
+        if (w1.x <= tm.x) a0 += b1;
+        if (w1.y <= tm.y) a1 += b1;
+        if (w1.z <= tm.z) a2 += b1;
+        if (w1.w <= tm.w) a3 += b1;
     }
     acc[0] = a0;
     acc[1] = a1;
@@ -171,14 +173,14 @@ __device__ __forceinline__ void sweep_half2(uint32_t mask, uint64_t aa, uint64_t
         const PhiloxSet p = ps[s];
         const uint4 wa = philox_xa(aa, p, rk);
         const uint4 wb = philox_xa(ab, p, rk);
-        if (wa.x <= ta.x) a0 |= bit;
-        if (wa.y <= ta.y) a1 |= bit;
-        if (wa.z <= ta.z) a2 |= bit;
-        if (wa.w <= ta.w) a3 |= bit;
-        if (wb.x <= tb.x) b0 |= bit;
-        if (wb.y <= tb.y) b1 |= bit;
-        if (wb.z <= tb.z) b2 |= bit;
-        if (wb.w <= tb.w) b3 |= bit;
+        if (wa.x <= ta.x) a0 += bit;
+        if (wa.y <= ta.y) a1 += bit;
+        if (wa.z <= ta.z) a2 += bit;
+        if (wa.w <= ta.w) a3 += bit;
+        if (wb.x <= tb.x) b0 += bit;
+        if (wb.y <= tb.y) b1 += bit;
+        if (wb.z <= tb.z) b2 += bit;
+        if (wb.w <= tb.w) b3 += bit;
     }
     acc_a[0] = a0;
     acc_a[1] = a1;
