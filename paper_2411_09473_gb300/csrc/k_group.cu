@@ -105,14 +105,14 @@ __device__ __forceinline__ void sweep_half(uint32_t mask, uint64_t a, uint4 tm, 
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     while (mask) {
         const int s1 = 31 - __clz(mask);
-        mask ^= 1u << s1;
         const uint32_t b1 = 1u << s1;
+        mask -= b1;  // b1 is set in mask: the same as clearing it
         const uint4 w1 = philox_xa(a, ps[s1], rk);
         if (kGroupChains == 2) {
             const bool two = mask != 0;
             const int s2 = two ? 31 - __clz(mask) : s1;
             const uint32_t b2 = two ? 1u << s2 : 0u;
-            mask ^= b2;
+            mask -= b2;
             const uint4 w2 = philox_xa(a, ps[s2], rk);
             if (w2.x <= tm.x) a0 += b2;
             if (w2.y <= tm.y) a1 += b2;
@@ -169,7 +169,7 @@ __device__ __forceinline__ void sweep_half2(uint32_t mask, uint64_t aa, uint64_t
     while (mask) {
         const int s = 31 - __clz(mask);
         const uint32_t bit = 1u << s;
-        mask ^= bit;
+        mask -= bit;  // bit is set in mask: the same as clearing it
         const PhiloxSet p = ps[s];
         const uint4 wa = philox_xa(aa, p, rk);
         const uint4 wb = philox_xa(ab, p, rk);
