@@ -95,6 +95,20 @@ def test_fuzz_small_graphs(imm, case):
     check_stream(imm, ctx, g, int(rng.integers(1, 3000)), seed)
 
 
+@pytest.mark.parametrize("case", range(6))
+def test_fuzz_ic_large_sets_both_paths(imm, large_path, case):
+    # random IC graphs dense enough for many sets past the warp's 256
+    # members: n not a multiple of 32, groups of a handful of sets, sets of
+    # a few hundred members next to sets of most of the graph
+    rng = np.random.default_rng(2000 + case)
+    n = int(rng.integers(300, 3000))
+    m = int(rng.integers(3 * n, 10 * n))
+    g = rand_graph(n, m, 50 + case, IC)
+    ctx = new_ctx(imm, g)
+    seed = int(rng.integers(0, 2**63))
+    check_stream(imm, ctx, g, int(rng.integers(200, 1500)), seed)
+
+
 @pytest.mark.parametrize("n,m,gseed,pmax", [(3000, 24000, 11, 0.3), (1 << 14, 1 << 17, 12, 0.1),
                                             (5000, 20000, 13, 1.0)])
 def test_ic_rmat_giant_sets(imm, large_path, n, m, gseed, pmax):
