@@ -304,7 +304,7 @@ DevGraph dev_graph(imm_ctx* c)
     g.row = P<uint64_t>(c->row);
     g.src = P<uint32_t>(c->src);
     g.thr = P<uint32_t>(c->thr);
-    g.guide = P<uint32_t>(c->guide);
+    g.guide = P<uint4>(c->guide);
     return g;
 }
 
@@ -362,8 +362,9 @@ int load_graph_common(imm_ctx* c, uint32_t n, uint64_t m, const void* row, const
         return set_err(c, IMM_EINVAL, "LT in-weights of some head sum to more than 1 + 1e-6");
     }
     if (model == IMM_LT) {
-        TRY(dalloc(c, c->guide, m_pad * 4));
-        CK(launch_lt_guide(P<uint64_t>(c->row), P<uint32_t>(c->thr), n, P<uint32_t>(c->guide), c->stream));
+        TRY(dalloc(c, c->guide, m_pad * 16));
+        CK(launch_lt_guide(P<uint64_t>(c->row), P<uint32_t>(c->thr), P<uint32_t>(c->src), n, P<uint4>(c->guide),
+                           c->stream));
     }
     c->n = n;
     c->m = m;

@@ -132,8 +132,9 @@ struct DevGraph {
     const uint64_t* row;  // n+1 in-edge offsets (CSR of G^T)
     const uint32_t* src;  // m (padded to a multiple of 4): tail of each in-edge
     const uint32_t* thr;  // m (padded, zeros): IC threshold or LT cumulative threshold
-    const uint32_t* guide;  // LT only, m: guide[row[v] + b] = first in-edge j of v with
-                            // cthr[j] > ceil(b * 2^24 / indeg(v)), b < indeg(v)
+    const uint4* guide;     // LT only, m: guide[row[v] + b] = (j, cthr[j], src[j], 0) for j the first
+                            // in-edge of v with cthr[j] > ceil(b * 2^24 / indeg(v)), b < indeg(v)
+                            // ((row[v+1], 0, 0, 0) when there is none)
 };
 
 // Counters and flags of one sampling batch (device memory, zeroed per batch
@@ -237,7 +238,8 @@ cudaError_t launch_validate_graph(const uint64_t* row, const uint32_t* src, cons
                                   uint64_t m, int model, int* d_flags, cudaStream_t st);
 cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, uint64_t m, int model,
                               uint32_t* thr, int* d_flags, cudaStream_t st);
-cudaError_t launch_lt_guide(const uint64_t* row, const uint32_t* cthr, uint32_t n, uint32_t* guide, cudaStream_t st);
+cudaError_t launch_lt_guide(const uint64_t* row, const uint32_t* cthr, const uint32_t* src, uint32_t n, uint4* guide,
+                            cudaStream_t st);
 
 // sampling
 uint32_t small_cap(int model);  // members a small-path set may hold (staging per set)

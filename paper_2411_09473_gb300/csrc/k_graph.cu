@@ -85,11 +85,14 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
 
 // LT guide table (index-assisted inverse transform; Chen & Asau 1974): for a
 // head v of in-degree d, bucket b < d covers the 24-bit draws r with
-// floor(r * d / 2^24) = b, whose smallest is lo_b = ceil(b * 2^24 / d), and
-// guide[row[v] + b] = first j with cthr[j] > lo_b.  A draw r in bucket b then
-// finds the first j with r < cthr[j] by scanning forward from guide[.]:
-// the same answer as a search over all of v's in-edges, in ~1-2 reads.
-__global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, uint32_t n, uint32_t* guide)
+// floor(r * d / 2^24) = b, whose smallest is lo_b = ceil(b * 2^24 / d).  The
+// entry of bucket b is (j, cthr[j], src[j], 0) for j = the first in-edge of v
+// with cthr[j] > lo_b.  A draw r in bucket b has its answer (the first j with
+// r < cthr[j]) at that j whenever r < cthr[j], which the entry tells with its
+// tail in hand; otherwise the scan continues over cthr from j + 1.  The same
+// answer as a search over all of v's in-edges, usually in one read.
+__global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, const uint32_t* src, uint32_t n,
+                                uint4* guide)
 {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
@@ -99,14 +102,15 @@ __global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, uint3
         for (uint64_t b = 0; b < d; ++b) {
             const uint64_t lo = ((b << 24) + d - 1) / d;
             while (j < re && (uint64_t)cthr[j] <= lo) ++j;
-            guide[rs + b] = j;
+            guide[rs + b] = j < re ? make_uint4(j, cthr[j], src[j], 0u) : make_uint4(re, 0u, 0u, 0u);
         }
     }
 }
 
-cudaError_t launch_lt_guide(const uint64_t* row, const uint32_t* cthr, uint32_t n, uint32_t* guide, cudaStream_t st)
+cudaError_t launch_lt_guide(const uint64_t* row, const uint32_t* cthr, const uint32_t* src, uint32_t n,
+                            uint4* guide, cudaStream_t st)
 {
-    lt_guide_kernel<<<(n + 255) / 256, 256, 0, st>>>(row, cthr, n, guide);
+    lt_guide_kernel<<<(n + 255) / 256, 256, 0, st>>>(row, cthr, src, n, guide);
     return cudaGetLastError();
 }
 

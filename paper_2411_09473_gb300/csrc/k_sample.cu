@@ -619,14 +619,22 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 // ===========================================================================
 constexpr int kLtThreads = 128;
 
-// first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi: the
-// guide table gives a start no later than the answer, then a short scan
-__device__ __forceinline__ uint32_t lt_pick(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r)
+// first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi, and
+// its tail in *u: the guide entry of r's bucket is the answer when r is below
+// its threshold (tail included); otherwise a short scan follows
+__device__ __forceinline__ uint32_t lt_pick(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r, uint32_t* u)
 {
     if (hi == lo) return hi;
     const uint32_t d = hi - lo;
-    uint32_t j = __ldg(g.guide + lo + (uint32_t)(((uint64_t)r * d) >> 24));
+    const uint4 e = __ldg(g.guide + lo + (uint32_t)(((uint64_t)r * d) >> 24));
+    uint32_t j = e.x;
+    if (j < hi && r < e.y) {
+        *u = e.z;
+        return j;
+    }
+    if (j < hi) ++j;
     while (j < hi && r >= __ldg(g.thr + j)) ++j;
+    if (j < hi) *u = __ldg(g.src + j);
     return j;
 }
 
@@ -668,11 +676,10 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         const uint4 w = philox_x(v, ps, b.rk);
         uint32_t lo, hi;
         edge_range(g, v, lo, hi);
-        const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8);
-        bool stop = pick == hi;
         uint32_t u = 0;
+        const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8, &u);
+        bool stop = pick == hi;
         if (!stop) {
-            u = __ldg(g.src + pick);
             for (uint32_t i = 0; i < len; ++i)
                 if (path[i][tid] == u) {
                     stop = true;
@@ -742,9 +749,9 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                 const uint4 w = philox_x(v, ps, b.rk);
                 uint32_t lo, hi;
                 edge_range(g, v, lo, hi);
-                const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8);
+                uint32_t u = 0;
+                const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8, &u);
                 if (pick == hi) break;
-                const uint32_t u = __ldg(g.src + pick);
                 const uint32_t bit = 1u << (u & 31);
                 if (bm[u >> 5] & bit) break;
                 bm[u >> 5] |= bit;
