@@ -619,22 +619,37 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 // ===========================================================================
 constexpr int kLtThreads = 128;
 
-// first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi, and
-// its tail in *u: the guide entry of r's bucket is the answer when r is below
-// its threshold (tail included); otherwise a short scan follows
-__device__ __forceinline__ uint32_t lt_pick(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r, uint32_t* u)
+// One step of the reverse walk at a vertex with in-edge range [lo, hi): the
+// first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi; the
+// tail u of j and u's in-edge range [*ulo, *uhi).  The guide entry of r's
+// bucket is the answer when r is below its threshold, and it carries u and
+// (in-degree below 127) u's range; otherwise a short scan and row reads.
+constexpr uint32_t kCthrMask = (1u << 25) - 1;
+
+__device__ __forceinline__ uint32_t lt_step(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r, uint32_t* u,
+                                            uint32_t* ulo, uint32_t* uhi)
 {
     if (hi == lo) return hi;
     const uint32_t d = hi - lo;
     const uint4 e = __ldg(g.guide + lo + (uint32_t)(((uint64_t)r * d) >> 24));
     uint32_t j = e.x;
-    if (j < hi && r < e.y) {
+    if (j < hi && r < (e.y & kCthrMask)) {
         *u = e.z;
+        const uint32_t du = e.y >> 25;
+        if (du < 127) {
+            *ulo = e.w;
+            *uhi = e.w + du;
+        } else {
+            edge_range(g, e.z, *ulo, *uhi);
+        }
         return j;
     }
     if (j < hi) ++j;
     while (j < hi && r >= __ldg(g.thr + j)) ++j;
-    if (j < hi) *u = __ldg(g.src + j);
+    if (j < hi) {
+        *u = __ldg(g.src + j);
+        edge_range(g, *u, *ulo, *uhi);
+    }
     return j;
 }
 
@@ -646,7 +661,7 @@ lt_small_kernel(DevGraph g, SampleBatch b)
     const int lane = tid & 31;
     const uint32_t ltm = lanemask_lt();
     bool busy = false, done = false;
-    uint32_t rel = 0, len = 0, v = 0;
+    uint32_t rel = 0, len = 0, v = 0, lo = 0, hi = 0;  // walk position and its in-edge range
     PhiloxSet ps{};
     for (;;) {
         const uint32_t need = __ballot_sync(kFull, !busy && !done);
@@ -663,6 +678,7 @@ lt_small_kernel(DevGraph g, SampleBatch b)
                     const uint64_t s = b.base + rel;
                     ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
                     v = draw_root(b.rk, s, g.n);
+                    edge_range(g, v, lo, hi);
                     path[0][tid] = v;
                     len = 1;
                 } else {
@@ -672,12 +688,10 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         }
         if (__all_sync(kFull, done)) break;
         if (!busy) continue;
-        // one step of the reverse walk at v
+        // one step of the reverse walk at v (in-edges [lo, hi))
         const uint4 w = philox_x(v, ps, b.rk);
-        uint32_t lo, hi;
-        edge_range(g, v, lo, hi);
-        uint32_t u = 0;
-        const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8, &u);
+        uint32_t u = 0, ulo = 0, uhi = 0;
+        const uint32_t pick = lt_step(g, lo, hi, w.x >> 8, &u, &ulo, &uhi);
         bool stop = pick == hi;
         if (!stop) {
             for (uint32_t i = 0; i < len; ++i)
@@ -696,6 +710,8 @@ lt_small_kernel(DevGraph g, SampleBatch b)
                 path[len][tid] = u;
                 ++len;
                 v = u;
+                lo = ulo;
+                hi = uhi;
             }
         } else {
             b.set_edges[rel] = len;
@@ -742,21 +758,23 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
         if (lane == 0) {
             const PhiloxSet ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
             uint32_t v = draw_root(b.rk, s, g.n);
+            uint32_t lo, hi;
+            edge_range(g, v, lo, hi);
             q[0] = v;
             bm[v >> 5] |= 1u << (v & 31);
             len = 1;
             for (;;) {
                 const uint4 w = philox_x(v, ps, b.rk);
-                uint32_t lo, hi;
-                edge_range(g, v, lo, hi);
-                uint32_t u = 0;
-                const uint32_t pick = lt_pick(g, lo, hi, w.x >> 8, &u);
+                uint32_t u = 0, ulo = 0, uhi = 0;
+                const uint32_t pick = lt_step(g, lo, hi, w.x >> 8, &u, &ulo, &uhi);
                 if (pick == hi) break;
                 const uint32_t bit = 1u << (u & 31);
                 if (bm[u >> 5] & bit) break;
                 bm[u >> 5] |= bit;
                 q[len++] = u;
                 v = u;
+                lo = ulo;
+                hi = uhi;
             }
             b.set_edges[rel] = len;
         }
