@@ -415,9 +415,12 @@ __device__ void team_cover(const SelectState& s, uint32_t j, Team t)
 }
 
 // Streams without bitmap-stored sets (small sets: decrementing is always the
-// cheaper update): cover and decrement in one pass, each warp removing the
-// members of the sets it has just covered, so a round needs one grid
-// barrier less.  Counts are identical to cover-then-decrement.
+// cheaper update): cover and decrement in one pass, so a round needs one grid
+// barrier less; counts are identical to cover-then-decrement.  A segment of
+// the picked vertex's inverted list with few entries per warp of the team
+// goes one entry per warp (the set's members strided over the lanes), so the
+// round's covered sets spread over all warps; a long one goes 32 entries per
+// warp with the members of those sets flattened across the lanes.
 template <class Team>
 __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t)
 {
@@ -427,32 +430,58 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t)
         s.picked[v] = 1;
         s.seeds[j] = v;
     }
-    const uint64_t lane = threadIdx.x & 31;
-    const uint64_t wfirst = t.rank() - lane, tsize = t.size();
-    unsigned long long vol = 0;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gw = t.rank() >> 5, nw = t.size() >> 5;
+    unsigned long long vol = 0, nnew = 0;
     for (uint32_t g = 0; g < s.nsegs; ++g) {
         const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
         const uint32_t* inv = s.segs[g].inv;
-        for (uint64_t i0 = a + wfirst; i0 < b; i0 += tsize) {
-            const uint64_t i = i0 + lane;
-            uint64_t start = 0;
-            uint32_t len = 0;
-            bool take = false;
-            if (i < b) {
-                const uint32_t sid = inv[i];
-                if (!s.covered[sid]) {
-                    s.covered[sid] = 1;
-                    take = true;
-                    start = s.off[sid];
-                    len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+        if (b - a <= 4 * nw) {
+            for (uint64_t i = a + gw; i < b; i += nw) {
+                uint32_t take = 0;
+                uint64_t start = 0;
+                uint32_t len = 0;
+                if (lane == 0) {
+                    const uint32_t sid = inv[i];
+                    if (!s.covered[sid]) {
+                        s.covered[sid] = 1;
+                        take = 1;
+                        start = s.off[sid];
+                        len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                    }
+                }
+                take = __shfl_sync(kFull, take, 0);
+                if (!take) continue;
+                start = shfl64s(start, 0);
+                len = __shfl_sync(kFull, len, 0);
+                for (uint32_t x = lane; x < len; x += 32) atomicAdd(&s.work[s.arena[start + x]], 0xFFFFFFFFu);
+                if (lane == 0) {
                     vol += len;
+                    ++nnew;
                 }
             }
-            const uint32_t bal = __ballot_sync(kFull, take);
-            if (lane == 0 && bal) atomicAdd(&s.newly_n[j], (unsigned long long)__popc(bal));
-            if (bal) warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);  // += -1
+        } else {
+            for (uint64_t i0 = a + gw * 32; i0 < b; i0 += nw * 32) {
+                const uint64_t i = i0 + lane;
+                uint64_t start = 0;
+                uint32_t len = 0;
+                bool take = false;
+                if (i < b) {
+                    const uint32_t sid = inv[i];
+                    if (!s.covered[sid]) {
+                        s.covered[sid] = 1;
+                        take = true;
+                        start = s.off[sid];
+                        len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                        vol += len;
+                        ++nnew;
+                    }
+                }
+                if (__any_sync(kFull, take)) warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);
+            }
         }
     }
+    if (nnew) atomicAdd(&s.newly_n[j], nnew);
     if (vol) {
         atomicAdd(&s.vol_cov[j], vol);
         atomicAdd(&s.vol_list[j], vol);
