@@ -575,8 +575,8 @@ def run_served(args, dist: Dist):
             "config": {"workload": f"{n} queries, Poisson {args.served_rate:g}/s, 8 resident R-MAT graphs "
                                    "2^16..2^20 (avg deg 16, IC/LT alternating, w=1/indeg), k=U{10..200}, "
                                    "eps=U(0.1,0.5), stream seed 5", "parallelism": f"replicas x{dist.world}"},
-            "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
-                           "max": float(lats.max()), "mean": float(lats.mean())},
+            "latency_ms": ({"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
+                            "max": float(lats.max()), "mean": float(lats.mean())} if len(lats) else None),
             "offered_rate": args.served_rate, "completed": int(len(lat)), "failed": int(failed),
             "submitted": int(i), "time_limited": bool(len(lat) + failed < n),
             "one_at_a_time": {"value": m / solo_s, "unit": "queries/s", "queries": m,

@@ -98,7 +98,9 @@ constexpr uint32_t kSmallCap = 256;          // members a warp keeps before hand
 constexpr int kSmallHashBits = 9;
 constexpr uint32_t kSmallHash = 1u << kSmallHashBits;  // > kSmallCap + 4*32 (one inner step)
 
-constexpr uint32_t kLtCap = 48;               // path length a lane keeps before handing off
+constexpr uint32_t kLtCap = 160;              // path length a lane keeps before handing off
+                                              // (its revisit test scans the path: a few hundred
+                                              // compares cost less than a step's memory reads)
 
 uint32_t small_cap(int model)
 {
@@ -617,7 +619,7 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 // ===========================================================================
 // LT, small path: one lane per walk, path kept in shared memory.
 // ===========================================================================
-constexpr int kLtThreads = 128;
+constexpr int kLtThreads = 64;  // path[kLtCap][kLtThreads] stays within static shared memory
 
 // One step of the reverse walk at a vertex with in-edge range [lo, hi): the
 // first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi; the
