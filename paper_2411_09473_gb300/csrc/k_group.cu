@@ -16,7 +16,9 @@
 //   scan    a dense pass over fn merges every nonzero fn[v] into vis[v],
 //           clears it and lists v with F = fn[v] for the next expansion:
 //           vertices with >= 32 in-edge quads in a large list with a running
-//           count of 64-quad chunks, the others in a small list.
+//           count of 64-quad chunks, the others in a small list with their
+//           offsets in the level's small quads (and, for each window of 32
+//           of those quads, its first vertex).
 // vis changes only in scan steps, so expansions read it without races.  The
 // giant sets of a power-law graph walk the same high-degree core within a
 // level or two of each other, so the per-vertex work (edge range, threshold
@@ -25,11 +27,11 @@
 //
 // The kernel is persistent (cooperative launch, one 1024-thread CTA per SM)
 // and advances in steps separated by grid barriers; warps claim work items
-// from one counter.  Expansion items are 32-vertex chunks of the small list,
-// whose quads are flattened across lanes (one quad per lane, its owner found
-// from per-warp run records in shared memory), and 64-quad chunks of the
-// large vertices, two quads per lane sharing each set's bookkeeping (owner
-// found by a 32-way search over the chunk prefix).
+// from one counter.  Expansion items are windows of 32 of the small
+// vertices' quads, one quad per lane (its owner found from per-warp run
+// records in shared memory), and 64-quad chunks of the large vertices, two
+// quads per lane sharing each set's bookkeeping (owner found by a 32-way
+// search over the chunk prefix).
 //
 // When no vertex is listed, two dense passes over vis give every set its
 // size and in-edge sum, reserve its output (member list, or an n-bit bitmap
