@@ -93,9 +93,9 @@ __device__ __forceinline__ bool reserve_small(const SampleBatch& b, uint32_t rel
 // ===========================================================================
 // IC, small path: one warp per set.
 // ===========================================================================
-constexpr int kSmallWarps = 8;
-constexpr uint32_t kSmallCap = 256;          // members a warp keeps before handing off
-constexpr int kSmallHashBits = 9;
+constexpr int kSmallWarps = 6;               // 7 KB of shared memory per warp
+constexpr uint32_t kSmallCap = 512;          // members a warp keeps before handing off
+constexpr int kSmallHashBits = 10;
 constexpr uint32_t kSmallHash = 1u << kSmallHashBits;  // > kSmallCap + 4*32 (one inner step)
 
 constexpr uint32_t kLtCap = 160;              // path length a lane keeps before handing off

@@ -97,7 +97,7 @@ def test_fuzz_small_graphs(imm, case):
 
 @pytest.mark.parametrize("case", range(6))
 def test_fuzz_ic_large_sets_both_paths(imm, large_path, case):
-    # random IC graphs dense enough for many sets past the warp's 256
+    # random IC graphs dense enough for many sets past the warp's 512
     # members: n not a multiple of 32, groups of a handful of sets, sets of
     # a few hundred members next to sets of most of the graph
     rng = np.random.default_rng(2000 + case)
@@ -183,7 +183,7 @@ def test_ic_global_bitmap_path(imm, large_path):
     imm.imm_sample(ctx, IC, theta, 31)
     off, mem = imm.imm_get_sets(ctx, 0, theta)
     sizes = np.diff(off.astype(np.int64))
-    big = np.nonzero(sizes > 256)[0]
+    big = np.nonzero(sizes > 512)[0]
     assert len(big) > 10
     o = oracle_for(g)
     rng = np.random.default_rng(0)
@@ -204,7 +204,7 @@ def test_ic_large_output_overflow_resamples(imm, large_path, monkeypatch):
     ctx = new_ctx(imm, g)
     check_stream(imm, ctx, g, 700, 43)
     off, _ = imm.imm_get_sets(ctx, 0, 700)
-    assert (np.diff(off.astype(np.int64)) > 256).sum() > 50
+    assert (np.diff(off.astype(np.int64)) > 512).sum() > 50
 
 
 def test_ic_group_ragged_groups_lists_and_bitmaps(imm, monkeypatch):
@@ -216,7 +216,7 @@ def test_ic_group_ragged_groups_lists_and_bitmaps(imm, monkeypatch):
     imm.imm_sample(ctx, IC, 300, 41)
     check_stream(imm, ctx, g, 2600, 41)
     off, _ = imm.imm_get_sets(ctx, 0, 2600)
-    assert (np.diff(off.astype(np.int64)) > 256).sum() > 130
+    assert (np.diff(off.astype(np.int64)) > 512).sum() > 130
     # disjoint directed cycles with p = 1 in n = 2^15: a set rooted on a cycle
     # is the whole cycle (one BFS level per member), stored as a list below
     # n/32 = 1024 members and as a bitmap above; sparse random edges elsewhere
