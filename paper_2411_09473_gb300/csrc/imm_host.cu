@@ -399,6 +399,45 @@ int ensure_slots(imm_ctx* c, uint32_t want_slots, bool need_bitmap)
     return IMM_OK;
 }
 
+// Cooperative kernels (the grouped sampler, the whole-grid selection) each
+// need every SM at once.  Two of them running side by side (contexts driven
+// from different host threads) could each hold SMs the other's CTAs wait
+// for, so on every device they run one after another: a launch waits for
+// the event recorded after the previous one.  Other kernels overlap freely.
+struct CoopOrder {
+    std::mutex mu;
+    cudaEvent_t last = nullptr;
+};
+
+CoopOrder& coop_order(int device)
+{
+    static std::mutex table_mu;
+    static std::unordered_map<int, CoopOrder*> table;
+    std::lock_guard<std::mutex> lk(table_mu);
+    CoopOrder*& o = table[device];
+    if (!o) o = new CoopOrder();  // lives for the process
+    return *o;
+}
+
+// Runs `launch` (which enqueues one cooperative kernel on st) after every
+// cooperative kernel enqueued before it on this device.
+template <class F>
+cudaError_t coop_launch(int device, cudaStream_t st, F&& launch)
+{
+    CoopOrder& o = coop_order(device);
+    std::lock_guard<std::mutex> lk(o.mu);
+    if (!o.last) {
+        const cudaError_t e = cudaEventCreateWithFlags(&o.last, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    } else {
+        const cudaError_t e = cudaStreamWaitEvent(st, o.last, 0);
+        if (e != cudaSuccess) return e;
+    }
+    const cudaError_t le = launch();
+    if (le != cudaSuccess) return le;
+    return cudaEventRecord(o.last, st);
+}
+
 // Scratch of the grouped IC large path (carved from one buffer; the masks
 // start at zero and every launch leaves them zero).
 int ensure_group(imm_ctx* c, GroupScratch* gs)
@@ -619,7 +658,7 @@ int batch_phase2(imm_ctx* c)
             GroupScratch gs;
             TRY(ensure_group(c, &gs));
             CK(cudaEventRecord(c->ev[2], c->stream));
-            CK(launch_ic_group(g, b, gs, c->di, c->stream));
+            CK(coop_launch(c->device, c->stream, [&] { return launch_ic_group(g, b, gs, c->di, c->stream); }));
             CK(cudaEventRecord(c->ev[3], c->stream));
         } else {
             const uint32_t want_slots = std::min<uint32_t>(
@@ -873,7 +912,8 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
         CK(launch_select_batch(P<SelectState>(c->dstate), dk, 1, c->di, c->stream));
         c->acc_launches += 1;
     } else {
-        const cudaError_t ce = launch_select_all(s, k, c->di, c->stream);
+        const cudaError_t ce =
+            coop_launch(c->device, c->stream, [&] { return launch_select_all(s, k, c->di, c->stream); });
         if (ce == cudaErrorCooperativeLaunchTooLarge || ce == cudaErrorNotSupported) {
             cudaGetLastError();
             for (uint32_t j = 0; j < k; ++j) CK(launch_select_round(s, j, c->di, c->stream, &c->acc_launches));
