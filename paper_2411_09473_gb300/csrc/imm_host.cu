@@ -865,6 +865,11 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out)
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
+    // IMM_SELECT_MODE=decrement|rebuild (tests): one counter update for every
+    // round; the two give the same counts (Sec. IV-C), which the tests check
+    s.force_mode = 0;
+    if (const char* fm = std::getenv("IMM_SELECT_MODE"))
+        s.force_mode = std::strcmp(fm, "decrement") == 0 ? 1 : std::strcmp(fm, "rebuild") == 0 ? 2 : 0;
     return IMM_OK;
 }
 

@@ -330,6 +330,7 @@ struct SelectState {
     uint32_t* seeds;     // k
     const DevSegment* segs;
     uint32_t nsegs;
+    int force_mode;      // 0: decrement or recount chosen per round; 1: always decrement; 2: always recount
 };
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
                                 uint64_t* launches);

@@ -81,6 +81,8 @@ __device__ __forceinline__ void warp_apply_sets(const uint32_t* arena, uint64_t 
 // uncovered bitmap + n/8 + sets/8.
 __device__ int round_mode(const SelectState& s, uint32_t j)
 {
+    if (s.force_mode == 1) return kModeDecrement;
+    if (s.force_mode == 2) return kModeRebuild;
     uint64_t before_list = 0, before_b = 0;
     for (uint32_t i = 0; i < j; ++i) {
         before_list += s.vol_list[i];
@@ -597,7 +599,7 @@ __device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_m
     for (uint32_t j = 0; j < k; ++j) {
         team_argmax(s, j, t, s_red);
         t.sync();
-        if (s.nbmp == 0) {
+        if (s.nbmp == 0 && s.force_mode != 2) {
             team_cover_decrement(s, j, t);
             t.sync();
             continue;

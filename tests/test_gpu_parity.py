@@ -257,6 +257,23 @@ def test_select_matches_oracle(imm, model, k):
     assert np.array_equal(seeds, want) and cov == wcov
 
 
+@pytest.mark.parametrize("mode", ["decrement", "rebuild"])
+def test_select_decrement_equals_rebuild(imm, monkeypatch, mode):
+    # the counter update of every round forced to one form (Sec. IV-C's
+    # adaptive update only picks the cheaper of two that give the same
+    # counts): seeds and coverage must be the oracle's either way, with
+    # bitmap-stored giant sets (IC) and short list-stored walks (LT)
+    monkeypatch.setenv("IMM_SELECT_MODE", mode)
+    for g, theta, seed in ((graphgen.make_graph(1 << 13, 1 << 16, 61, IC, "uniform", pmax=0.25), 1200, 61),
+                           (graphgen.make_graph(1 << 12, 1 << 15, 62, LT, "inv_indeg"), 3000, 62)):
+        ctx = new_ctx(imm, g)
+        o = check_stream(imm, ctx, g, theta, seed)
+        for k in (1, 7, 60):
+            seeds, cov = imm.imm_select(ctx, k)
+            want, wcov = o.select(k)
+            assert np.array_equal(seeds, want) and cov == wcov
+
+
 def test_select_k_equals_n_and_empty_stream(imm):
     g = rand_graph(40, 120, 5, IC)
     ctx = new_ctx(imm, g)
