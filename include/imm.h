@@ -278,9 +278,9 @@ int imm_set_arena_limit(imm_ctx* ctx, uint64_t bytes);
  * another framework whose memory pool owns the whole GPU, or a service whose
  * memory footprint is fixed when it starts.
  *
- * Same greedy max coverage as imm_select (Alg. 2: k rounds, ties to the
- * lowest vertex id, picked vertices excluded, picking continues at count 0),
- * over a set system the caller already holds on the device:
+ * Same greedy max coverage as imm_select (k rounds, ties to the lowest vertex
+ * id, picked vertices excluded, picking continues at count 0), over a set
+ * system the caller already holds on the device:
  *   d_off      device uint64[nsets + 1], member offsets (nondecreasing, d_off[0] = 0)
  *   d_members  device uint32[d_off[nsets]], vertex ids < n, distinct within a set
  *   d_seeds_out   device uint32[k]: the picks in order
@@ -292,13 +292,21 @@ int imm_set_arena_limit(imm_ctx* ctx, uint64_t bytes);
  * (about 9 MB), held on every GPU that loads the library until the process
  * exits.  Limits: n <= IMM_NOALLOC_MAX_N, nsets <= IMM_NOALLOC_MAX_SETS,
  * k <= IMM_NOALLOC_MAX_K.
- * The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  Every
- * call shares the array and clears what must start at zero; calls that
- * overlap on the GPU (other streams, other host threads) race on it and must
- * be serialised by the caller.
+ * The first call on a device looks up that array's device address and the
+ * device's SM count (with the device current) and keeps them for the life of
+ * the process; make that first call before any stream capture, and do not
+ * call it again after a cudaDeviceReset of that device.  Every call shares
+ * the array and clears what must start at zero; calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.
+ * A member id >= n is never used as an index: the kernels skip it, and the
+ * call then writes 0xFFFFFFFF to every seed and 2^64 - 1 to *d_covered_out
+ * (the check happens on the GPU, so it cannot be returned as a status).
+ * A launch error pending on the calling thread from earlier work is cleared
+ * on entry.
  * Errors: EINVAL (n == 0, k == 0, k > n, a size above its limit, a NULL
- * required pointer), ECUDA (device lookup or launch failed). */
+ * required pointer), ECUDA (device lookup or a launch failed; no later round
+ * is enqueued after a failed launch). */
 #define IMM_NOALLOC_MAX_N    (1u << 20)
 #define IMM_NOALLOC_MAX_SETS (1u << 22)
 #define IMM_NOALLOC_MAX_K    4096u

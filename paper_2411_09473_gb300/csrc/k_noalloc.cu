@@ -31,6 +31,7 @@ constexpr uint64_t kOffPicked = kOffCounts + kMaxN * 4;              // uint8[kM
 constexpr uint64_t kOffCovered = kOffPicked + kMaxN;                 // uint8[kMaxSets]
 constexpr uint64_t kOffKeys = kOffCovered + kMaxSets;                // uint64[kMaxK]
 constexpr uint64_t kOffTotal = kOffKeys + kMaxK * 8;                 // uint64
+constexpr uint64_t kOffBad = kOffTotal + 8;                          // uint32: a member id >= n was seen
 constexpr uint64_t kScratchBytes = kOffTotal + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -41,15 +42,18 @@ struct Scratch {
     uint8_t* covered;
     unsigned long long* keys;
     unsigned long long* total;
+    uint32_t* bad;
 };
 
-// Device address of g_scratch, looked up once per device (with that device
-// current); the host-side symbol itself is not a device address.
+// Device address of g_scratch and the SM count, looked up once per device
+// (with that device current); the host-side symbol itself is not a device
+// address.  The cached address is not refreshed after a device reset.
 std::mutex g_mu;
 void* g_addr[256];
+unsigned g_sms[256];
 bool g_ready[256];
 
-int scratch_for_current_device(Scratch* s)
+int scratch_for_current_device(Scratch* s, unsigned* sms)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
@@ -59,19 +63,24 @@ int scratch_for_current_device(Scratch* s)
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_ready[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
+        int count = 0;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr ||
+            cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count <= 0) {
             cudaGetLastError();
             return IMM_ECUDA;
         }
         g_addr[dev] = p;
+        g_sms[dev] = (unsigned)count;
         g_ready[dev] = true;
     }
+    *sms = g_sms[dev];
     unsigned char* base = static_cast<unsigned char*>(g_addr[dev]);
     s->counts = reinterpret_cast<uint32_t*>(base + kOffCounts);
     s->picked = base + kOffPicked;
     s->covered = base + kOffCovered;
     s->keys = reinterpret_cast<unsigned long long*>(base + kOffKeys);
     s->total = reinterpret_cast<unsigned long long*>(base + kOffTotal);
+    s->bad = reinterpret_cast<uint32_t*>(base + kOffBad);
     return IMM_OK;
 }
 
@@ -85,18 +94,26 @@ __global__ void na_clear_kernel(Scratch s, uint32_t n, uint64_t nsets, uint32_t 
     }
     for (uint64_t i = t; i < nsets; i += stride) s.covered[i] = 0;
     for (uint64_t i = t; i < k; i += stride) s.keys[i] = 0;
-    if (t == 0) *s.total = 0;
+    if (t == 0) {
+        *s.total = 0;
+        *s.bad = 0;
+    }
 }
 
-// occurrence counts: one atomic increment per member
-__global__ void na_count_kernel(Scratch s, uint64_t nsets, const uint64_t* off, const uint32_t* mem)
+// occurrence counts: one atomic increment per member; a member id >= n is
+// not counted and raises the `bad` flag
+__global__ void na_count_kernel(Scratch s, uint32_t n, uint64_t nsets, const uint64_t* off, const uint32_t* mem)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t set = gw; set < nsets; set += nw) {
         const uint64_t a = off[set], b = off[set + 1];
-        for (uint64_t i = a + lane; i < b; i += 32) atomicAdd(&s.counts[mem[i]], 1u);
+        for (uint64_t i = a + lane; i < b; i += 32) {
+            const uint32_t u = mem[i];
+            if (u < n) atomicAdd(&s.counts[u], 1u);
+            else *s.bad = 1;
+        }
     }
 }
 
@@ -132,8 +149,8 @@ __global__ void na_argmax_kernel(Scratch s, uint32_t n, uint32_t j)
 }
 
 // every uncovered set holding the pick: mark covered, decrement its members
-__global__ void na_cover_kernel(Scratch s, uint64_t nsets, const uint64_t* off, const uint32_t* mem, uint32_t j,
-                                uint32_t* seeds_out)
+__global__ void na_cover_kernel(Scratch s, uint32_t n, uint64_t nsets, const uint64_t* off, const uint32_t* mem,
+                                uint32_t j, uint32_t* seeds_out)
 {
     const uint32_t v = 0xFFFFFFFFu - (uint32_t)s.keys[j];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -153,7 +170,10 @@ __global__ void na_cover_kernel(Scratch s, uint64_t nsets, const uint64_t* off, 
             has = __any_sync(kFull, i < b && mem[i] == v);
         }
         if (!has) continue;
-        for (uint64_t i = a + lane; i < b; i += 32) atomicSub(&s.counts[mem[i]], 1u);
+        for (uint64_t i = a + lane; i < b; i += 32) {
+            const uint32_t u = mem[i];
+            if (u < n) atomicSub(&s.counts[u], 1u);
+        }
         if (lane == 0) {
             s.covered[set] = 1;
             ++covered;
@@ -162,9 +182,14 @@ __global__ void na_cover_kernel(Scratch s, uint64_t nsets, const uint64_t* off, 
     if (lane == 0 && covered) atomicAdd(s.total, covered);
 }
 
-__global__ void na_finish_kernel(Scratch s, unsigned long long* covered_out)
+// the covered total; a set system with a member id >= n gets the error
+// pattern instead (every seed 0xFFFFFFFF, covered 2^64 - 1)
+__global__ void na_finish_kernel(Scratch s, uint32_t k, uint32_t* seeds_out, unsigned long long* covered_out)
 {
-    if (covered_out) *covered_out = *s.total;
+    const bool bad = *s.bad != 0;
+    if (bad)
+        for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) seeds_out[j] = 0xFFFFFFFFu;
+    if (covered_out && threadIdx.x == 0) *covered_out = bad ? ~0ull : *s.total;
 }
 
 }  // namespace
@@ -176,25 +201,25 @@ extern "C" int imm_select_noalloc(uint32_t n, uint64_t nsets, const uint64_t* d_
     using namespace imm;
     if (n == 0 || n > kMaxN || nsets > kMaxSets || k == 0 || k > n || k > kMaxK) return IMM_EINVAL;
     if (!d_off || !d_seeds_out || (nsets > 0 && !d_members)) return IMM_EINVAL;
+    // a launch error left by earlier, unrelated work on this host thread is
+    // cleared here, so that it is not reported as this call's failure
+    cudaGetLastError();
     Scratch s;
-    const int rc = scratch_for_current_device(&s);
+    unsigned sms = 0;
+    const int rc = scratch_for_current_device(&s, &sms);
     if (rc != IMM_OK) return rc;
-    cudaDeviceProp prop;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return IMM_ECUDA;
-    }
-    const unsigned sms = (unsigned)prop.multiProcessorCount;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     na_clear_kernel<<<sms * 4, 256, 0, st>>>(s, n, nsets, k);
-    if (nsets) na_count_kernel<<<sms * 8, 256, 0, st>>>(s, nsets, d_off, d_members);
+    if (nsets) na_count_kernel<<<sms * 8, 256, 0, st>>>(s, n, nsets, d_off, d_members);
+    if (cudaGetLastError() != cudaSuccess) return IMM_ECUDA;
     unsigned ab = (n + 255) / 256;
     if (ab > sms * 4) ab = sms * 4;
     for (uint32_t j = 0; j < k; ++j) {
         na_argmax_kernel<<<ab, 256, 0, st>>>(s, n, j);
-        na_cover_kernel<<<sms * 8, 256, 0, st>>>(s, nsets, d_off, d_members, j, d_seeds_out);
+        na_cover_kernel<<<sms * 8, 256, 0, st>>>(s, n, nsets, d_off, d_members, j, d_seeds_out);
+        // a failed launch stops the call before the later rounds are enqueued
+        if (cudaGetLastError() != cudaSuccess) return IMM_ECUDA;
     }
-    na_finish_kernel<<<1, 1, 0, st>>>(s, d_covered_out);
+    na_finish_kernel<<<1, 256, 0, st>>>(s, k, d_seeds_out, d_covered_out);
     return cudaGetLastError() == cudaSuccess ? IMM_OK : IMM_ECUDA;
 }
