@@ -148,12 +148,16 @@ PLAIN = {
                   ell=1.0, seed=3,
                   desc="LT, R-MAT 4,194,304 vertices / 67,108,864 edges, w=1/indeg, k=100, "
                        "eps=0.5"),
+    # the paper's IC weight law (p ~ U[0, 1]) with its k = 50, eps = 0.5
+    "ic_u1_256k": dict(n=1 << 18, m=1 << 22, model=IC, weights="uniform", pmax=1.0, k=50, epsilon=0.5,
+                       ell=1.0, seed=6,
+                       desc="IC, R-MAT 262,144 vertices / 4,194,304 edges, p~U[0,1], k=50, eps=0.5"),
 }
 
 
 def plain_workload(name: str) -> Workload:
     p = PLAIN[name]
-    g = make_graph(p["n"], p["m"], p["seed"], p["model"], p["weights"])
+    g = make_graph(p["n"], p["m"], p["seed"], p["model"], p["weights"], p.get("pmax", 0.1))
     return Workload(name=name, graph=g, k=p["k"], epsilon=p["epsilon"], ell=p["ell"],
                     seed=p["seed"], desc=p["desc"])
 

@@ -239,24 +239,17 @@ __device__ __forceinline__ void sweep_two(const DevGraph& g, const PhiloxKeys& r
     mask_invalid(lb, vb);
 }
 
-// Apply the live bits of one quad per lane: bits u has not been expanded for
-// are ored into fn[u] (no value returned: nothing waits on it).  The four
-// lookups of a lane are independent, so the visit costs one memory round
-// trip.
-__device__ __forceinline__ void visit_quad(const unsigned long long* vis, unsigned long long* fn,
-                                           const QuadLive& ql)
+// Apply the live bits of one quad per lane: they are ored into fn[u] with no
+// value returned, so nothing waits on the visit.  Bits of sets that have
+// already reached u are dropped by the next scan step, which lists u only
+// with the sets it is new to.
+__device__ __forceinline__ void visit_quad(unsigned long long* fn, const QuadLive& ql)
 {
     const uint32_t u[4] = {ql.src.x, ql.src.y, ql.src.z, ql.src.w};
-    unsigned long long m[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) m[t] = ((unsigned long long)ql.hi[t] << 32) | ql.lo[t];
-    unsigned long long known[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) known[t] = m[t] ? __ldcg(vis + u[t]) : ~0ull;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        m[t] &= ~known[t];
-        if (m[t]) atomicOr(fn + u[t], m[t]);
+        const unsigned long long m = ((unsigned long long)ql.hi[t] << 32) | ql.lo[t];
+        if (m) atomicOr(fn + u[t], m);
     }
 }
 
@@ -324,20 +317,25 @@ constexpr uint32_t kWordsPerItem = 8;     // bitmap words per extraction item
 constexpr uint32_t kScanPerItem = 256;    // vertices per scan item
 constexpr uint32_t kSlotOffset = 2;       // steps by which slot k starts after slot k - 1
 
-// Scan of vertices [v0, v0 + kScanPerItem): every vertex with new bits F has
-// them merged into vis and cleared from fn, and is listed for expansion
-// unless it has no in-edges.
+// Scan of vertices [v0, v0 + kScanPerItem): every vertex with bits in fn has
+// fn cleared; the sets among them that had not reached it yet (F) are merged
+// into vis, and the vertex is listed for their expansion unless it has no
+// in-edges.
 __device__ __forceinline__ void scan_item(const DevGraph& g, const SlotArrays& a, uint32_t par, uint32_t v0,
                                           uint32_t lane)
 {
     for (uint32_t r = 0; r < kScanPerItem; r += 32) {
         const uint32_t v = v0 + r + lane;
-        const unsigned long long F = v < g.n ? __ldcg(a.fn + v) : 0ull;
+        unsigned long long F = v < g.n ? __ldcg(a.fn + v) : 0ull;
         if (!__any_sync(kFull, F != 0ull)) continue;
-        uint32_t rs = 0, re = 0, nq = 0;
         if (F) {
             __stcg(a.fn + v, 0ull);
-            __stcg(a.vis + v, __ldcg(a.vis + v) | F);
+            const unsigned long long old = __ldcg(a.vis + v);
+            F &= ~old;
+            if (F) __stcg(a.vis + v, old | F);
+        }
+        uint32_t rs = 0, re = 0, nq = 0;
+        if (F) {
             range_of(g, v, rs, re);
             nq = nquads(rs, re);
             if (nq >= kGroupHeavyQ) {
@@ -393,11 +391,11 @@ __device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& 
     if (__any_sync(kFull, hb)) {
         QuadLive lb = {};
         if (ha) sweep_two(g, rk, ps, qa, qb, hb, e.x, e.y, F, la, lb);
-        visit_quad(a.vis, a.fn, la);
-        visit_quad(a.vis, a.fn, lb);
+        visit_quad(a.fn, la);
+        visit_quad(a.fn, lb);
     } else {
         if (ha) sweep_quad(g, rk, ps, qa, e.x, e.y, F, la);
-        visit_quad(a.vis, a.fn, la);
+        visit_quad(a.fn, la);
     }
 }
 
@@ -437,7 +435,7 @@ __device__ __forceinline__ void window_item(const DevGraph& g, const PhiloxKeys&
         const uint32_t quad = (r.x >> 2) + (j - r.z);
         sweep_quad(g, rk, ps, quad, r.x, r.y, recF[pos], ql);
     }
-    visit_quad(a.vis, a.fn, ql);
+    visit_quad(a.fn, ql);
     __syncwarp();
 }
 

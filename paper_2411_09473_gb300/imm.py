@@ -294,14 +294,17 @@ def imm_get_set(ctx: _Ctx, set_id: int, cap: int) -> np.ndarray:
     return buf[: ln.value].copy()
 
 
-def imm_get_sets(ctx: _Ctx, first: int, count: int):
-    """Sets first .. first+count-1: (offsets relative to the first set, members)."""
+def imm_get_sets(ctx: _Ctx, first: int, count: int, members: bool = True):
+    """Sets first .. first+count-1: (offsets relative to the first set,
+    members); with members=False only the offsets (a call with cap 0)."""
     lib = _load()
     off = np.zeros(count + 1, dtype=np.uint64)
     rc = lib.imm_get_sets(ctx.handle, first, count, off.ctypes.data, None, 0)
     total = int(off[-1])
     if rc != IMM_OK and total == 0:
         _check(ctx, rc)
+    if not members:
+        return off, None
     mem = np.zeros(max(total, 1), dtype=np.uint32)
     _check(ctx, lib.imm_get_sets(ctx.handle, first, count, off.ctypes.data, mem.ctypes.data, total))
     return off, mem[:total]

@@ -40,3 +40,41 @@ def edges_to_graph(n, edges, weights, model):
 
 def oracle_for(g):
     return oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+
+
+def load_golden(name):
+    """Stored oracle results written by tests/golden/make_golden.py."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".json")) as f:
+        return json.load(f)
+
+
+def graph_digest(g) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for a in (g.row.astype("<u8"), g.src.astype("<u4"), g.weight.astype("<f4")):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()
+
+
+def counts_digest(cnt) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(np.asarray(cnt).astype("<u4")).tobytes()).hexdigest()
+
+
+def assert_run_equals_golden(seeds, st, rec, what=""):
+    """Every field of one IMM run (Alg. 1) against the oracle's stored run:
+    seeds in pick order, the theta ladder with per-round coverage, LB, theta,
+    stream size, coverage, total members, lambda' and lambda* (bit for bit)."""
+    assert [int(x) for x in seeds] == rec["seeds"], what
+    assert st.rounds == rec["rounds"] and st.stopped_early == rec["stopped_early"], what
+    r = st.rounds
+    assert [int(st.theta_i[i]) for i in range(r)] == rec["theta_i"], what
+    assert [int(st.covered_i[i]) for i in range(r)] == rec["covered_i"], what
+    assert [int(st.sets_i[i]) for i in range(r)] == rec["sets_i"], what
+    assert float(st.lb).hex() == rec["lb_hex"], what
+    assert st.theta == rec["theta"] and st.num_sets == rec["num_sets"], what
+    assert st.covered == rec["covered"] and st.members == rec["members"], what
+    assert float(st.lambda_prime).hex() == rec["lambda_prime_hex"], what
+    assert float(st.lambda_star).hex() == rec["lambda_star_hex"], what

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import graphgen
-from gpu_common import oracle_for
+from gpu_common import assert_run_equals_golden, graph_digest, load_golden, oracle_for
 
 pytestmark = pytest.mark.gpu
 
@@ -73,3 +73,23 @@ def test_batch_rejects_bad_queries(imm):
         imm.imm_run_batch([(ctx, 0, 0.5, 1.0, 1)])
     with pytest.raises(imm.ImmError):
         imm.imm_run_batch([(ctx, 5, 1.5, 1.0, 1)])
+
+
+def test_batch64_equals_oracle_runs(imm):
+    """The batched workload at its full size (64 instances, n up to 2^18,
+    IC/LT alternating, k 5..100, eps 0.1..0.5): every instance equals the
+    oracle's own run of it, stored by tests/golden/make_golden.py."""
+    gold = load_golden("batch64")
+    b = graphgen.batch_workload(count=gold["count"], max_log_n=gold["max_log_n"])
+    ctxs = [load(imm, g) for g in b.graphs]
+    queries = [(ctxs[q.graph_id], q.k, q.epsilon, q.ell, q.seed) for q in b.queries]
+    seeds, stats, status = imm.imm_run_batch(queries)
+    assert status == [0] * len(queries)
+    for i, q in enumerate(b.queries):
+        rec = gold["instances"][i]
+        g = b.graphs[q.graph_id]
+        assert graph_digest(g) == rec["graph_sha256"], i
+        assert (q.k, q.epsilon.hex(), q.seed) == (rec["k"], rec["epsilon_hex"], rec["seed"]), i
+        assert_run_equals_golden(seeds[i], stats[i], rec, f"instance {i}")
+    for c in ctxs:
+        imm.imm_destroy(c)

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import graphgen
+from gpu_common import assert_run_equals_golden, graph_digest, load_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -94,3 +95,43 @@ def test_served_memory_bound_admission_still_drains(imm):
         gid, k, eps, ell, seed = ids[qid]
         s2, _ = imm.imm_run(ctx, g.model, k, eps, ell, seed)
         assert np.array_equal(res[0], s2)
+
+
+def test_served_stream_equals_oracle_runs(imm):
+    """The first queries of the served workload (8 resident R-MAT graphs of
+    2^16..2^20 vertices, Poisson arrivals at 200/s, k 10..200, eps 0.1..0.5),
+    replayed at their arrival times against a server with the benchmark's
+    settings: every result equals the oracle's own run of the query, stored by
+    tests/golden/make_golden.py."""
+    gold = load_golden("served")
+    graphs = graphgen.served_graphs()
+    for g, rec in zip(graphs, gold["graphs"]):
+        assert graph_digest(g) == rec["graph_sha256"]
+    ctxs = [load(imm, g) for g in graphs]
+    qs = graphgen.served_queries()[: gold["queries"]]
+    srv = imm.imm_server_create(ctxs, memory_budget_bytes=96 << 30, max_active=128)
+    ids, got = {}, {}
+    t0 = time.perf_counter()
+    i = 0
+    deadline = t0 + 600
+    while len(got) < len(qs) and time.perf_counter() < deadline:
+        now = time.perf_counter() - t0
+        while i < len(qs) and qs[i].arrival_s <= now:
+            q = qs[i]
+            ids[imm.imm_server_submit(srv, q.graph_id, q.k, q.epsilon, q.ell, q.seed)] = i
+            i += 1
+        for (qid, status, _, _) in imm.imm_server_poll(srv):
+            assert status == 0, status
+            j = ids[qid]
+            got[j] = imm.imm_server_take(srv, qid, qs[j].k)
+        time.sleep(0.001)
+    assert len(got) == len(qs)
+    imm.imm_server_destroy(srv)
+    for j, q in enumerate(qs):
+        rec = gold["results"][j]
+        assert (q.graph_id, q.k, q.epsilon.hex(), q.seed) == (rec["graph_id"], rec["k"], rec["epsilon_hex"],
+                                                               rec["seed"]), j
+        seeds, st = got[j]
+        assert_run_equals_golden(seeds, st, rec, f"query {j}")
+    for c in ctxs:
+        imm.imm_destroy(c)
