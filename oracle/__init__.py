@@ -27,6 +27,15 @@ Parity status per function (what pins it, tests/test_oracle_*.py):
   run (fresh_final)   same ladder as the plain run; final stream is exactly
                       theta sets equal to an independent sample under the
                       second key; RIS identity of its covered fraction
+  opim_params         theta_max * k equals lambda* of Tang et al.'s bound at
+                      the same confidence (OPT >= k); i_max against theta ratio
+  opim_bounds         lower bound below the exact spread (world enumeration)
+                      and upper bound above the exact optimum (brute force)
+                      over many independent collections, and both within a
+                      stated factor of the truth at large theta
+  opim_run            collections double; R1 is the plain stream, R2 the
+                      stream under seed ^ OPIM_KEY; stop rule on alpha; the
+                      returned set's spread meets 1 - 1/e - eps of OPT
 """
 from __future__ import annotations
 
@@ -72,6 +81,25 @@ class Stats(ctypes.Structure):
     ]
 
 
+class OpimStats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_uint32),
+        ("stopped_early", ctypes.c_uint32),
+        ("i_max", ctypes.c_uint32),
+        ("sets_i", ctypes.c_uint64 * 64),
+        ("cov1_i", ctypes.c_uint64 * 64),
+        ("cov2_i", ctypes.c_uint64 * 64),
+        ("upper_i", ctypes.c_double * 64),
+        ("lower_i", ctypes.c_double * 64),
+        ("theta_max", ctypes.c_double),
+        ("theta_0", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+    ]
+
+
+OPIM_KEY = 0xD1B54A32D192ED03  # key of the second RR collection: seed ^ OPIM_KEY
+
+
 def _load():
     global _lib
     if _lib is not None:
@@ -100,6 +128,9 @@ def _load():
         "orc_get_counts": ([vp, vp], None),
         "orc_get_arena": ([vp, vp, vp], None),
         "orc_get_thresholds": ([vp, vp], None),
+        "orc_opim_params": ([u32, u32, f64, f64, vp], None),
+        "orc_opim_bounds": ([u32, u32, f64, f64, u64, u64, u64, vp], None),
+        "orc_opim_run": ([vp, u32, f64, f64, u64, vp, ctypes.POINTER(OpimStats)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -143,6 +174,22 @@ def theta_params(n: int, k: int, eps: float, ell: float) -> dict:
     _load().orc_theta_params(n, k, eps, ell, _p(out))
     return dict(ell_p=out[0], eps_p=out[1], lnC=out[2], lambda_prime=out[3],
                 lambda_star=out[4], alpha=out[5], beta=out[6], rounds=int(out[7]))
+
+
+def opim_params(n: int, k: int, eps: float, ell: float) -> dict:
+    """OPIM-C's constants (delta = n^-ell): theta_max, theta_0, i_max, a1, a2."""
+    out = np.zeros(7, dtype=np.float64)
+    _load().orc_opim_params(n, k, eps, ell, _p(out))
+    return dict(delta=out[0], lnC=out[1], theta_max=out[2], theta_0=out[3], i_max=int(out[4]), a1=out[5],
+                a2=out[6])
+
+
+def opim_bounds(n: int, k: int, a1: float, a2: float, theta: int, cov1: int, cov2: int):
+    """(upper bound on OPT from R1 coverage, lower bound on the spread of the
+    greedy's set from its R2 coverage)."""
+    out = np.zeros(2, dtype=np.float64)
+    _load().orc_opim_bounds(n, k, a1, a2, theta, cov1, cov2, _p(out))
+    return float(out[0]), float(out[1])
 
 
 def select_sets(n: int, off: np.ndarray, mem: np.ndarray, k: int):
@@ -210,6 +257,17 @@ class Oracle:
         rc = _load().orc_run_ex(self._h, k, eps, ell, seed, 1 if fresh_final else 0, _p(seeds), ctypes.byref(st))
         if rc != OK:
             raise ValueError(f"orc_run -> {rc}")
+        return seeds, st
+
+    def opim_run(self, k: int, eps: float, ell: float, seed: int):
+        """OPIM-style early stop (OPIM-C of Tang et al. 2018, which Sec. VI
+        cites): R1 (key seed) and R2 (key seed ^ OPIM_KEY) double each round
+        until the lower / upper bound ratio reaches 1 - 1/e - eps."""
+        seeds = np.zeros(k, dtype=np.uint32)
+        st = OpimStats()
+        rc = _load().orc_opim_run(self._h, k, eps, ell, seed, _p(seeds), ctypes.byref(st))
+        if rc != OK:
+            raise ValueError(f"orc_opim_run -> {rc}")
         return seeds, st
 
     @property

@@ -463,6 +463,157 @@ int orc_run(orc_ctx* c, uint32_t k, double eps, double ell, uint64_t seed, uint3
     return orc_run_ex(c, k, eps, ell, seed, 0u, seeds, st);
 }
 
+/* ------------------------------------------------------------------ */
+/* OPIM-style early stop (Sec. VI cites OPIM: Tang, Tang, Xiao, Yuan,   */
+/* SIGMOD 2018, whose OPIM-C procedure this follows).  Two independent  */
+/* RR-set collections of equal size, R1 (key seed) and R2 (key seed xor */
+/* ORC_OPIM_KEY), double each round; the greedy picks S on R1; R1's     */
+/* coverage gives an upper confidence bound on OPT and R2's coverage of */
+/* S a lower confidence bound on the spread of S; sampling stops once   */
+/* their ratio reaches 1 - 1/e - eps (or at the last round).            */
+/* Readings where the paper (which only cites OPIM) is silent:          */
+/*   - the failure probability is delta = n^-ell (IMM's ell);           */
+/*   - theta_0 is rounded up; round i holds ceil(theta_0) * 2^(i-1)     */
+/*     sets per collection; i_max = max(1, ceil(log2(theta_max /       */
+/*     theta_0)));                                                      */
+/*   - the bound on the optimum's R1 coverage is the greedy's coverage  */
+/*     over 1 - (1 - 1/k)^k (OPIM-C's tighter marginal-gain bound is    */
+/*     not used);                                                       */
+/*   - R2's key is seed xor ORC_OPIM_KEY (an odd constant).             */
+/* ------------------------------------------------------------------ */
+#define ORC_OPIM_KEY 0xD1B54A32D192ED03ull
+
+/* out: [0] delta, [1] ln C(n,k), [2] theta_max, [3] theta_0, [4] i_max,
+ *      [5] a1, [6] a2 */
+void orc_opim_params(uint32_t n, uint32_t k, double eps, double ell, double out[7])
+{
+    const double nd = (double)n;
+    const double ln_n = log(nd);
+    const double delta = exp(-ell * ln_n);
+    double lnC = 0.0;
+    for (uint32_t i = 1; i <= k; i++) lnC += log((double)(n - k + i)) - log((double)i);
+    const double g = 1.0 - 1.0 / ORC_E;
+    const double l6 = log(6.0 / delta);
+    const double t = g * sqrt(l6) + sqrt(g * (lnC + l6));
+    const double theta_max = 2.0 * nd * t * t / (eps * eps * (double)k);
+    const double theta_0 = theta_max * eps * eps * (double)k / nd;
+    double im = ceil(log2(theta_max / theta_0));
+    if (im < 1.0) im = 1.0;
+    const double a2 = log(3.0 * im / delta);
+    out[0] = delta;
+    out[1] = lnC;
+    out[2] = theta_max;
+    out[3] = theta_0;
+    out[4] = im;
+    out[5] = a2 + lnC;
+    out[6] = a2;
+}
+
+/* Confidence bounds of one round: cov1 = R1 coverage of the greedy's set,
+ * cov2 = its R2 coverage, theta = sets per collection.
+ * out: [0] upper bound on OPT, [1] lower bound on the set's spread. */
+void orc_opim_bounds(uint32_t n, uint32_t k, double a1, double a2, uint64_t theta, uint64_t cov1, uint64_t cov2,
+                     double out[2])
+{
+    const double nd = (double)n, th = (double)theta;
+    const double ratio = 1.0 - pow(1.0 - 1.0 / (double)k, (double)k);
+    const double lam_u = (double)cov1 / ratio;
+    const double up = sqrt(lam_u + a1 / 2.0) + sqrt(a1 / 2.0);
+    const double lo = sqrt((double)cov2 + 2.0 * a2 / 9.0) - sqrt(a2 / 2.0);
+    out[0] = up * up * nd / th;
+    out[1] = (lo * lo - a2 / 18.0) * nd / th;
+}
+
+typedef struct {
+    uint32_t rounds;
+    uint32_t stopped_early;   /* 1 if the ratio test fired before the last round */
+    uint32_t i_max;
+    uint64_t sets_i[64];      /* sets per collection in round i */
+    uint64_t cov1_i[64];      /* R1 coverage of the greedy's set */
+    uint64_t cov2_i[64];      /* R2 coverage of the same set */
+    double upper_i[64];
+    double lower_i[64];
+    double theta_max;
+    double theta_0;
+    double alpha;             /* lower / upper of the last round */
+} orc_opim_stats;
+
+int orc_opim_run(orc_ctx* c, uint32_t k, double eps, double ell, uint64_t seed, uint32_t* seeds,
+                 orc_opim_stats* st)
+{
+    if (k == 0 || k > c->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0)) return ORC_EINVAL;
+    double prm[7];
+    orc_opim_params(c->n, k, eps, ell, prm);
+    const double theta_max = prm[2], theta_0 = prm[3], a1 = prm[5], a2 = prm[6];
+    const uint32_t i_max = (uint32_t)prm[4];
+    const double t0 = ceil(theta_0);
+    if (t0 * ldexp(1.0, (int)i_max - 1) >= 4294967295.0) return ORC_EINVAL;
+    /* R2: a second context on the same graph (thresholds copied) */
+    orc_ctx* r2 = (orc_ctx*)calloc(1, sizeof(orc_ctx));
+    if (!r2) return ORC_ENOMEM;
+    r2->n = c->n; r2->m = c->m; r2->model = c->model;
+    r2->row = (uint64_t*)malloc(((uint64_t)c->n + 1) * sizeof(uint64_t));
+    r2->src = (uint32_t*)malloc((c->m ? c->m : 1) * sizeof(uint32_t));
+    r2->thr = (uint32_t*)malloc((c->m ? c->m : 1) * sizeof(uint32_t));
+    r2->cnt = (uint32_t*)calloc(c->n, sizeof(uint32_t));
+    r2->visited = (uint8_t*)calloc(c->n, 1);
+    r2->queue = (uint32_t*)malloc((uint64_t)c->n * sizeof(uint32_t));
+    r2->cap_sets = 1024;
+    r2->off = (uint64_t*)malloc((r2->cap_sets + 1) * sizeof(uint64_t));
+    r2->cap_mem = 1 << 16;
+    r2->mem = (uint32_t*)malloc(r2->cap_mem * sizeof(uint32_t));
+    if (!r2->row || !r2->src || !r2->thr || !r2->cnt || !r2->visited || !r2->queue || !r2->off || !r2->mem) {
+        orc_destroy(r2);
+        return ORC_ENOMEM;
+    }
+    memcpy(r2->row, c->row, ((uint64_t)c->n + 1) * sizeof(uint64_t));
+    if (c->m) memcpy(r2->src, c->src, c->m * sizeof(uint32_t));
+    if (c->m) memcpy(r2->thr, c->thr, c->m * sizeof(uint32_t));
+    r2->off[0] = 0;
+    orc_reset(c);
+    memset(st, 0, sizeof(*st));
+    st->i_max = i_max;
+    st->theta_max = theta_max;
+    st->theta_0 = theta_0;
+    uint8_t* in_s = (uint8_t*)calloc(c->n, 1);
+    if (!in_s) { orc_destroy(r2); return ORC_ENOMEM; }
+    int rc = ORC_OK;
+    for (uint32_t i = 1; i <= i_max; i++) {
+        const uint64_t theta = (uint64_t)(t0 * ldexp(1.0, (int)i - 1));
+        if ((rc = orc_sample(c, theta, seed)) != ORC_OK) break;
+        if ((rc = orc_sample(r2, theta, seed ^ ORC_OPIM_KEY)) != ORC_OK) break;
+        uint64_t cov1 = 0;
+        if ((rc = orc_select(c, k, seeds, &cov1)) != ORC_OK) break;
+        /* R2 coverage of the greedy's set: sets holding any of its members */
+        for (uint32_t j = 0; j < k; j++) in_s[seeds[j]] = 1;
+        uint64_t cov2 = 0;
+        for (uint64_t s = 0; s < r2->nsets; s++) {
+            for (uint64_t e = r2->off[s]; e < r2->off[s + 1]; e++)
+                if (in_s[r2->mem[e]]) { cov2++; break; }
+        }
+        for (uint32_t j = 0; j < k; j++) in_s[seeds[j]] = 0;
+        double b[2];
+        orc_opim_bounds(c->n, k, a1, a2, theta, cov1, cov2, b);
+        const double alpha = b[1] / b[0];
+        if (i - 1 < 64) {
+            st->sets_i[i - 1] = theta;
+            st->cov1_i[i - 1] = cov1;
+            st->cov2_i[i - 1] = cov2;
+            st->upper_i[i - 1] = b[0];
+            st->lower_i[i - 1] = b[1];
+        }
+        st->rounds = i;
+        st->alpha = alpha;
+        if (alpha >= 1.0 - 1.0 / ORC_E - eps) {
+            st->stopped_early = i < i_max ? 1u : 0u;
+            break;
+        }
+    }
+    free(in_s);
+    orc_destroy(r2);
+    return rc;
+}
+
 /* ---- accessors for tests ---- */
 uint64_t orc_num_sets(const orc_ctx* c) { return c->nsets; }
 uint64_t orc_num_members(const orc_ctx* c) { return c->off[c->nsets]; }
