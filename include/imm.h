@@ -175,6 +175,47 @@ int imm_run(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell,
 int imm_run_ex(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell,
                uint64_t rng_seed, uint32_t flags, uint32_t* seeds_out, imm_stats* stats_out);
 
+/* OPIM-style early stop (Sec. VI cites OPIM: Tang, Tang, Xiao, Yuan,
+ * SIGMOD 2018; this follows its OPIM-C procedure).  Two independent RR-set
+ * collections of equal size double each round: R1 is the context's stream
+ * under rng_seed, R2 a second stream on the same graph under rng_seed ^
+ * IMM_OPIM_KEY (held by the call, freed before it returns).  Per round i:
+ *   theta_i = ceil(theta_0) * 2^(i-1) sets per collection, i = 1 .. i_max;
+ *   S = the greedy's k picks over R1 (as imm_select), cov1 = its R1
+ *   coverage, cov2 = the number of R2 sets holding a member of S;
+ *   upper = (sqrt(cov1 / (1 - (1-1/k)^k) + a1/2) + sqrt(a1/2))^2 * n / theta_i
+ *   lower = ((sqrt(cov2 + 2 a2/9) - sqrt(a2/2))^2 - a2/18) * n / theta_i
+ *   stop with S once lower / upper >= 1 - 1/e - epsilon, or at i_max.
+ * With delta = n^-ell, g = 1 - 1/e, L = ln(6/delta):
+ *   theta_max = 2n (g sqrt(L) + sqrt(g (ln C(n,k) + L)))^2 / (eps^2 k),
+ *   theta_0 = theta_max eps^2 k / n, i_max = max(1, ceil(log2(theta_max /
+ *   theta_0))), a2 = ln(3 i_max / delta), a1 = a2 + ln C(n,k).
+ * Host fp64, no FMA contraction.  Writes k seeds to seeds_out (host) and, if
+ * stats_out != NULL, *stats_out; the context keeps R1 as its stream.
+ * Errors: EINVAL (k == 0, k > n, eps not in (0,1), ell <= 0, model differs
+ * from the graph's, collections would reach 2^32-1 sets), ESTATE, ENOMEM,
+ * ECUDA. */
+#define IMM_OPIM_KEY 0xD1B54A32D192ED03ull
+typedef struct imm_opim_stats {
+    uint32_t rounds;                  /* rounds run */
+    uint32_t stopped_early;           /* 1 if the ratio test fired before round i_max */
+    uint32_t i_max;
+    uint64_t sets_i[IMM_MAX_ROUNDS];  /* sets per collection in round i */
+    uint64_t cov1_i[IMM_MAX_ROUNDS];  /* R1 coverage of that round's picks */
+    uint64_t cov2_i[IMM_MAX_ROUNDS];  /* R2 coverage of the same picks */
+    double upper_i[IMM_MAX_ROUNDS];   /* upper confidence bound on OPT */
+    double lower_i[IMM_MAX_ROUNDS];   /* lower confidence bound on the picks' spread */
+    double theta_max;
+    double theta_0;
+    double alpha;                     /* lower / upper of the last round */
+    double ms_total;                  /* host wall time of the call */
+    double ms_sample;                 /* device time of R1's sampling kernels */
+    double ms_select;                 /* device time of the selections */
+    uint64_t kernel_launches;
+} imm_opim_stats;
+int imm_run_opim(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell, uint64_t rng_seed,
+                 uint32_t* seeds_out, imm_opim_stats* stats_out);
+
 /* One query of a batch: the context holding its graph (loaded with
  * imm_load_graph; the model is the graph's), and IMM's parameters. */
 typedef struct imm_query {

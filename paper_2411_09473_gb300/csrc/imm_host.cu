@@ -1460,6 +1460,122 @@ int imm_run_ex(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, ui
     return IMM_OK;
 }
 
+// OPIM-style early stop (Sec. VI cites OPIM, Tang et al. SIGMOD 2018; this
+// follows its OPIM-C procedure).  R1 is the context's own stream under
+// rng_seed; R2 lives in a worker context on the same graph under rng_seed ^
+// IMM_OPIM_KEY.  Both double each round; the greedy over R1 gives the seeds
+// and R1 coverage (upper confidence bound on OPT, the optimum's coverage
+// bounded by the greedy's over 1 - (1 - 1/k)^k), the seeds' R2 coverage gives
+// a lower confidence bound on their spread, and sampling stops once
+// lower / upper >= 1 - 1/e - eps.  delta = n^-ell.  Host fp64, no FMA
+// contraction, in the same operation order as any plain evaluation.
+int imm_run_opim(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, uint64_t rng_seed,
+                 uint32_t* seeds_out, imm_opim_stats* stats_out)
+{
+    if (!c) return IMM_EINVAL;
+    DeviceGuard guard(c->device);
+    const auto t0c = std::chrono::steady_clock::now();
+    if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
+    if (model != c->model) return set_err(c, IMM_EINVAL, "model %d differs from the loaded graph's", model);
+    if (k == 0 || k > c->n) return set_err(c, IMM_EINVAL, "k must be in [1, n]");
+    if (!(epsilon > 0.0 && epsilon < 1.0)) return set_err(c, IMM_EINVAL, "epsilon must be in (0, 1)");
+    if (!(ell > 0.0)) return set_err(c, IMM_EINVAL, "ell must be > 0");
+    if (!seeds_out) return set_err(c, IMM_EINVAL, "seeds_out is NULL");
+    const double nd = (double)c->n;
+    const double ln_n = std::log(nd);
+    const double delta = std::exp(-ell * ln_n);
+    double lnC = 0.0;
+    for (uint32_t i = 1; i <= k; i++) lnC += std::log((double)(c->n - k + i)) - std::log((double)i);
+    const double g = 1.0 - 1.0 / kE;
+    const double l6 = std::log(6.0 / delta);
+    const double tt = g * std::sqrt(l6) + std::sqrt(g * (lnC + l6));
+    const double theta_max = 2.0 * nd * tt * tt / (epsilon * epsilon * (double)k);
+    const double theta_0 = theta_max * epsilon * epsilon * (double)k / nd;
+    double im = std::ceil(std::log2(theta_max / theta_0));
+    if (im < 1.0) im = 1.0;
+    const double a2 = std::log(3.0 * im / delta);
+    const double a1 = a2 + lnC;
+    const uint32_t i_max = (uint32_t)im;
+    const double t0 = std::ceil(theta_0);
+    if (t0 * std::ldexp(1.0, (int)i_max - 1) >= 4294967295.0)
+        return set_err(c, IMM_EINVAL, "the last round's collections would reach 2^32-1 sets");
+    const double ratio = 1.0 - std::pow(1.0 - 1.0 / (double)k, (double)k);
+    const double target = 1.0 - 1.0 / kE - epsilon;
+
+    imm_opim_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.i_max = i_max;
+    st.theta_max = theta_max;
+    st.theta_0 = theta_0;
+    drop_stream(c);
+    reset_acc(c);
+    TRY(ensure(c, c->flags, 64));
+    imm_ctx* w = nullptr;
+    int rc = make_worker(c, &w);
+    uint64_t cov_launches = 0;
+    for (uint32_t i = 1; rc == IMM_OK && i <= i_max; i++) {
+        const uint64_t theta = (uint64_t)(t0 * std::ldexp(1.0, (int)i - 1));
+        rc = sample_to(c, theta, rng_seed);
+        if (rc == IMM_OK && (rc = sample_to(w, theta, rng_seed ^ IMM_OPIM_KEY)) != IMM_OK)
+            rc = set_err(c, rc, "second collection: %s", w->err.c_str());
+        uint64_t cov1 = 0, cov2 = 0;
+        if (rc == IMM_OK) rc = select_k(c, k, seeds_out, &cov1);
+        if (rc == IMM_OK) {
+            // the selection left picked[v] = 1 exactly for the k seeds
+            CoverageArgs a;
+            a.nsets = w->nsets;
+            a.words = (uint32_t)(((uint64_t)c->n + 31) / 32);
+            a.k = k;
+            a.off = P<uint64_t>(w->off);
+            a.arena = P<uint32_t>(w->arena);
+            a.set_bmp = P<uint32_t>(w->set_bmp);
+            a.bmp = P<uint32_t>(w->bmp);
+            a.flag = P<uint8_t>(c->picked);
+            a.seeds = P<uint32_t>(c->seeds);
+            a.out = P<unsigned long long>(c->flags);
+            cudaError_t e = launch_coverage(a, c->di, c->stream);
+            unsigned long long hc = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c->flags.p, 8, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = cuda_err(c, e, "seed-set coverage of the second collection");
+            cov2 = hc;
+            cov_launches += 1;
+        }
+        if (rc != IMM_OK) break;
+        const double th = (double)theta;
+        const double lam_u = (double)cov1 / ratio;
+        const double up = std::sqrt(lam_u + a1 / 2.0) + std::sqrt(a1 / 2.0);
+        const double lo = std::sqrt((double)cov2 + 2.0 * a2 / 9.0) - std::sqrt(a2 / 2.0);
+        const double upper = up * up * nd / th;
+        const double lower = (lo * lo - a2 / 18.0) * nd / th;
+        const double alpha = lower / upper;
+        if (i - 1 < IMM_MAX_ROUNDS) {
+            st.sets_i[i - 1] = theta;
+            st.cov1_i[i - 1] = cov1;
+            st.cov2_i[i - 1] = cov2;
+            st.upper_i[i - 1] = upper;
+            st.lower_i[i - 1] = lower;
+        }
+        st.rounds = i;
+        st.alpha = alpha;
+        if (alpha >= target) {
+            st.stopped_early = i < i_max ? 1u : 0u;
+            break;
+        }
+    }
+    if (w) {
+        st.kernel_launches = w->acc_launches;
+        destroy_worker(w);
+    }
+    if (rc != IMM_OK) return rc;
+    st.kernel_launches += c->acc_launches + cov_launches;
+    st.ms_sample = c->acc_sample_ms;
+    st.ms_select = c->acc_select_ms;
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0c).count();
+    if (stats_out) *stats_out = st;
+    return IMM_OK;
+}
+
 // Members of one stored set, sorted ascending (lists are sorted here, bitmaps
 // are expanded in id order).
 static int fetch_set(imm_ctx* c, uint64_t id, std::vector<uint32_t>& out)

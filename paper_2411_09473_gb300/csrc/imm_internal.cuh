@@ -341,4 +341,21 @@ cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo
 cudaError_t launch_select_batch(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,
                                 const DeviceInfo& di, cudaStream_t st);
 
+// Seed-set coverage of a stored stream (k_opim.cu): sets [0, nsets) holding
+// a vertex whose flag is nonzero (list-stored sets) or one of the k seeds
+// (bitmap-stored sets); the count goes to *out.
+struct CoverageArgs {
+    uint64_t nsets;
+    uint32_t words;
+    uint32_t k;
+    const uint64_t* off;
+    const uint32_t* arena;
+    const uint32_t* set_bmp;
+    const uint32_t* bmp;
+    const uint8_t* flag;      // [n] 1 for the seeds
+    const uint32_t* seeds;    // [k]
+    unsigned long long* out;
+};
+cudaError_t launch_coverage(const CoverageArgs& a, const DeviceInfo& di, cudaStream_t st);
+
 }  // namespace imm

@@ -62,6 +62,29 @@ class imm_stats(ctypes.Structure):
         return d
 
 
+class imm_opim_stats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_uint32),
+        ("stopped_early", ctypes.c_uint32),
+        ("i_max", ctypes.c_uint32),
+        ("sets_i", ctypes.c_uint64 * IMM_MAX_ROUNDS),
+        ("cov1_i", ctypes.c_uint64 * IMM_MAX_ROUNDS),
+        ("cov2_i", ctypes.c_uint64 * IMM_MAX_ROUNDS),
+        ("upper_i", ctypes.c_double * IMM_MAX_ROUNDS),
+        ("lower_i", ctypes.c_double * IMM_MAX_ROUNDS),
+        ("theta_max", ctypes.c_double),
+        ("theta_0", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_sample", ctypes.c_double),
+        ("ms_select", ctypes.c_double),
+        ("kernel_launches", ctypes.c_uint64),
+    ]
+
+
+IMM_OPIM_KEY = 0xD1B54A32D192ED03
+
+
 class imm_server_config(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32)]
 
@@ -111,6 +134,7 @@ def _load():
         "imm_select": ([vp, u32, vp, ctypes.POINTER(u64)], i32),
         "imm_run": ([vp, i32, u32, f64, f64, u64, vp, ctypes.POINTER(imm_stats)], i32),
         "imm_run_ex": ([vp, i32, u32, f64, f64, u64, u32, vp, ctypes.POINTER(imm_stats)], i32),
+        "imm_run_opim": ([vp, i32, u32, f64, f64, u64, vp, ctypes.POINTER(imm_opim_stats)], i32),
         "imm_reset_sets": ([vp], i32),
         "imm_stream_size": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
         "imm_get_set": ([vp, u64, vp, u32, ctypes.POINTER(u32)], i32),
@@ -251,6 +275,15 @@ def imm_run_ex(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_se
     st = imm_stats()
     _check(ctx, _load().imm_run_ex(ctx.handle, model, k, epsilon, ell, rng_seed, flags, seeds.ctypes.data,
                                    ctypes.byref(st)))
+    return seeds[:k], st
+
+
+def imm_run_opim(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_seed: int):
+    """OPIM-style early stop (OPIM-C): (seeds, imm_opim_stats)."""
+    seeds = np.zeros(max(k, 1), dtype=np.uint32)
+    st = imm_opim_stats()
+    _check(ctx, _load().imm_run_opim(ctx.handle, model, k, epsilon, ell, rng_seed, seeds.ctypes.data,
+                                     ctypes.byref(st)))
     return seeds[:k], st
 
 
