@@ -15,6 +15,7 @@ workloads and attaches them under "workloads" in the same JSON line:
   ic_wc_4k    IC, R-MAT 4,096 / 32,768, p = 1/indeg, k=10, eps=0.5
   ic_u1_256k  IC, R-MAT 262,144 / 4,194,304, p ~ U[0, 1], k=50, eps=0.5
               (the paper's IC weight law), with RRR-set coverage of V
+  opim_*      the OPIM-style early stop (imm_run_opim) on lt_4m and ic_u1_256k
   batch64     64 IMM instances through imm_run_batch (queries/s)
   served      10,000 Poisson queries at 200/s through imm_server (queries/s,
               p50/p99 latency)
@@ -536,6 +537,63 @@ def run_plain(args, dist: Dist, name: str, steps: int, warmup: int, e2e_on: bool
     return line
 
 
+def run_opim(args, dist: Dist, name: str, steps: int, warmup: int):
+    """OPIM-style early stop (imm_run_opim) on a plain workload: one step =
+    one whole run (two RR collections doubling until the bound ratio holds),
+    compared with the oracle's stored run."""
+    import torch
+
+    import graphgen
+    from paper_2411_09473_gb300 import imm
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = graphgen.plain_workload(name)
+    g = w.graph
+    ctx = imm.imm_create(device=dev, stream=stream)
+    imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, g.weight, g.model)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+    for _ in range(warmup):
+        seeds, st = imm.imm_run_opim(ctx, g.model, w.k, w.epsilon, w.ell, w.seed)
+    clocks = ClockSampler(dev)
+    torch.cuda.synchronize()
+    clocks.start()
+    evs, launches = [], 0
+    for _ in range(steps):
+        flush.fill_(2.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        seeds, st = imm.imm_run_opim(ctx, g.model, w.k, w.epsilon, w.ell, w.seed)
+        b.record(stream)
+        evs.append((a, b))
+        launches += int(st.kernel_launches)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    imm.imm_destroy(ctx)
+    r = st.rounds
+    parity = None
+    gold = golden("opim")
+    rec = next((x for x in gold["runs"] if x["workload"] == name), None) if gold else None
+    if rec is not None:
+        eq = ([int(x) for x in seeds] == rec["seeds"] and r == rec["rounds"]
+              and [int(st.cov1_i[i]) for i in range(r)] == rec["cov1_i"]
+              and [int(st.cov2_i[i]) for i in range(r)] == rec["cov2_i"]
+              and [float(st.upper_i[i]).hex() for i in range(r)] == rec["upper_hex"]
+              and [float(st.lower_i[i]).hex() for i in range(r)] == rec["lower_hex"])
+        parity = {"equal": bool(eq), "against": "tests/golden/opim.json (oracle run)"}
+    return {
+        "metric": "IMM seconds-to-seeds (OPIM-style early stop)", "value": ms / 1e3, "unit": "s",
+        "n_gpus": dist.world, "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": False,
+        "dtype": "u32", "data": "synthetic", "config": {"workload": w.desc},
+        "rounds": r, "i_max": int(st.i_max), "sets_per_collection": int(st.sets_i[r - 1]),
+        "alpha": st.alpha, "target": 1.0 - 1.0 / 2.718281828459045 - w.epsilon,
+        "parity": parity, "gpu_launches": launches, "clocks": clk,
+    }
+
+
 def run_batch(args, dist: Dist, steps: int, warmup: int):
     """64 independent IMM instances (R-MAT, n log-uniform over 2^10..2^18,
     average degree 8..32, IC/LT alternating, k 5..100, eps 0.1..0.5), one
@@ -743,6 +801,8 @@ def run_gpu(args, dist: Dist):
         es, ew = max(1, min(args.extra_steps, args.steps)), 3
         for name in ("lt_4m", "ic_wc_4k", "ic_u1_256k"):
             extra[name] = run_plain(args, dist, name, es, ew, False, not args.no_cpu_baseline, 10.0)
+        for name in ("lt_4m", "ic_u1_256k"):
+            extra["opim_" + name] = run_opim(args, dist, name, es, ew)
         extra["batch64"] = run_batch(args, dist, es, ew)
         extra["served"] = run_served(args, dist)
         line["workloads"] = extra

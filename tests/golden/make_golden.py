@@ -9,6 +9,7 @@ nothing in what each query computes.
     python tests/golden/make_golden.py ic_u01_1m     # ~2 h, ~43 GB RAM, one core
     python tests/golden/make_golden.py batch64       # 64 instances, n up to 2^18
     python tests/golden/make_golden.py served [N]    # the first N served queries
+    python tests/golden/make_golden.py opim          # OPIM early stop, LT and U[0,1] IC
 
 Each writes tests/golden/<name>.json.  Floating-point fields are also stored as
 float.hex() so that the tests compare them bit for bit.
@@ -129,6 +130,24 @@ def _served_one(i):
     return rec
 
 
+def _opim_one(name):
+    w = graphgen.plain_workload(name)
+    g = w.graph
+    o = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model)
+    t0 = time.perf_counter()
+    seeds, st = o.opim_run(w.k, w.epsilon, w.ell, w.seed)
+    dt = time.perf_counter() - t0
+    r = st.rounds
+    return dict(workload=name, k=w.k, epsilon=w.epsilon, ell=w.ell, seed=w.seed, graph_sha256=graph_digest(g),
+                seeds=[int(x) for x in seeds], rounds=int(r), stopped_early=int(st.stopped_early),
+                i_max=int(st.i_max), sets_i=[int(st.sets_i[i]) for i in range(r)],
+                cov1_i=[int(st.cov1_i[i]) for i in range(r)], cov2_i=[int(st.cov2_i[i]) for i in range(r)],
+                upper_hex=[float(st.upper_i[i]).hex() for i in range(r)],
+                lower_hex=[float(st.lower_i[i]).hex() for i in range(r)],
+                alpha_hex=float(st.alpha).hex(), theta_max_hex=float(st.theta_max).hex(),
+                theta_0_hex=float(st.theta_0).hex(), oracle_seconds=round(dt, 3))
+
+
 def _pool_map(fn, items, procs):
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
@@ -160,6 +179,12 @@ def make_served(count, procs):
                          results=recs))
 
 
+def make_opim(procs):
+    recs = _pool_map(_opim_one, ["lt_4m", "ic_u1_256k"], procs)
+    write("opim", dict(workload="opim", desc="OPIM-style early stop (OPIM-C) on the LT and U[0,1] IC workloads",
+                       generated_by="python tests/golden/make_golden.py opim", runs=recs))
+
+
 def main(argv):
     graphgen.build()
     oracle.build()
@@ -169,6 +194,8 @@ def main(argv):
         make_plain(what)
     elif what == "batch64":
         make_batch(procs)
+    elif what == "opim":
+        make_opim(procs)
     elif what == "served":
         make_served(int(argv[2]) if len(argv) > 2 else 300, procs)
     else:

@@ -110,3 +110,21 @@ def test_served_golden():
             seeds, st = oracle.Oracle(g.n, g.row, g.src, g.weight, g.model).run(q.k, q.epsilon, q.ell, q.seed)
             same_as_run(rec, seeds, st)
     assert cheap >= 1
+
+
+def test_opim_golden_bounds_and_stop_rule():
+    gold = load("opim")
+    for rec in gold["runs"]:
+        p = graphgen.PLAIN[rec["workload"]]
+        prm = oracle.opim_params(p["n"], p["k"], p["epsilon"], p["ell"])
+        assert rec["i_max"] == prm["i_max"] and rec["theta_max_hex"] == float(prm["theta_max"]).hex()
+        t0 = math.ceil(prm["theta_0"])
+        r = rec["rounds"]
+        assert rec["sets_i"] == [t0 << i for i in range(r)]
+        target = 1.0 - 1.0 / math.e - p["epsilon"]
+        for i in range(r):
+            up, low = oracle.opim_bounds(p["n"], p["k"], prm["a1"], prm["a2"], rec["sets_i"][i], rec["cov1_i"][i],
+                                         rec["cov2_i"][i])
+            assert (float(up).hex(), float(low).hex()) == (rec["upper_hex"][i], rec["lower_hex"][i])
+            assert (low / up >= target) == (i == r - 1) or (i == r - 1 == rec["i_max"] - 1)
+        assert len(rec["seeds"]) == p["k"] == len(set(rec["seeds"]))

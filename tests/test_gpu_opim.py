@@ -54,3 +54,26 @@ def test_opim_giant_bitmap_sets(imm):
     g = graphgen.make_graph(8192, 65536, 21, graphgen.IC, "uniform", pmax=0.6)
     st = same(imm, g, 10, 0.2, 1.0, 7)
     assert st.cov2_i[st.rounds - 1] > 0
+
+
+def test_opim_full_workloads_equal_oracle_runs(imm):
+    """lt_4m and ic_u1_256k at full size: every field of the oracle's stored
+    OPIM run (tests/golden/opim.json)."""
+    from gpu_common import graph_digest, load_golden
+    gold = load_golden("opim")
+    for rec in gold["runs"]:
+        w = graphgen.plain_workload(rec["workload"])
+        g = w.graph
+        assert graph_digest(g) == rec["graph_sha256"]
+        ctx = imm.imm_create(device=0)
+        imm.imm_load_graph(ctx, g.n, g.m, g.row, g.src, g.weight, g.model)
+        seeds, st = imm.imm_run_opim(ctx, g.model, w.k, w.epsilon, w.ell, w.seed)
+        r = st.rounds
+        assert [int(x) for x in seeds] == rec["seeds"] and r == rec["rounds"] and st.i_max == rec["i_max"]
+        assert [int(st.sets_i[i]) for i in range(r)] == rec["sets_i"]
+        assert [int(st.cov1_i[i]) for i in range(r)] == rec["cov1_i"]
+        assert [int(st.cov2_i[i]) for i in range(r)] == rec["cov2_i"]
+        assert [float(st.upper_i[i]).hex() for i in range(r)] == rec["upper_hex"]
+        assert [float(st.lower_i[i]).hex() for i in range(r)] == rec["lower_hex"]
+        assert float(st.alpha).hex() == rec["alpha_hex"] and st.stopped_early == rec["stopped_early"]
+        imm.imm_destroy(ctx)
