@@ -85,6 +85,8 @@ typedef struct imm_stats {
     uint64_t kernel_launches;             /* all kernel launches issued by the call */
     uint64_t sample_edges;                /* same as edges_examined, for the timed launches */
     uint64_t sample_members;              /* members produced by the timed sampler launches */
+    uint64_t reused_sets;                 /* served queries: sets already resident when the query
+                                             started (a stream drawn with the same seed) */
 } imm_stats;
 
 /* Create a context on CUDA device `device`.  `alloc` may be NULL (then
@@ -257,6 +259,16 @@ typedef struct imm_server imm_server;
 typedef struct imm_server_config {
     uint64_t memory_budget_bytes;
     uint32_t max_active;  /* 0 = 64 */
+    /* Nonzero: prefix-stable stream sharing.  A finished query's RRR-set
+     * stream stays resident in its idle worker, and a later query on the same
+     * graph with the same rng seed reuses it (Alg. 1 extends a stream by
+     * appending set ids, and a set is a function of graph, seed and set id
+     * only): its selections see the prefix of the resident stream that the
+     * query would have sampled, and it samples only the sets beyond it.
+     * Results are those of the query run alone; imm_stats.reused_sets counts
+     * the sets it found resident.  Resident streams count against the memory
+     * budget, and idle workers are reclaimed when admission needs memory. */
+    uint32_t share_streams;
 } imm_server_config;
 
 typedef struct imm_completion {

@@ -807,11 +807,15 @@ int sample_to(imm_ctx* c, uint64_t theta, uint64_t seed)
 // Find_Most_Influential_Set: buffers and state (prepare), one launch, and
 // the read-back of seeds and per-round coverage (collect).
 // ---------------------------------------------------------------------------
-int select_prepare(imm_ctx* c, uint32_t k, SelectState* out)
+// prefix < nsets: the selection sees only sets [0, prefix) of the stream
+// (the others start covered and the counts are those of the prefix), so its
+// result is that of a stream of `prefix` sets.
+int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~0ull)
 {
     if (!c->loaded) return set_err(c, IMM_ESTATE, "no graph loaded");
     if (k == 0 || k > c->n) return set_err(c, IMM_EINVAL, "k must be in [1, n]");
     const uint64_t R = c->nsets;
+    const bool part = prefix < R;
     TRY(ensure(c, c->work, (size_t)c->n * 4));
     TRY(ensure(c, c->picked, (size_t)c->n));
     TRY(ensure(c, c->covered, std::max<uint64_t>(R, 1)));
@@ -828,13 +832,23 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out)
     for (auto& sg : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(sg.voff), P<uint32_t>(sg.inv)});
     TRY(ensure(c, c->dsegs, std::max<size_t>(hsegs.size(), 1) * sizeof(DevSegment)));
 
+    uint64_t list_end = 0;
+    if (part) {
+        TRY(ensure(c, c->flags, 64));
+        CK(cudaMemcpyAsync(&c->pin->sc.list_members, P<uint64_t>(c->off) + prefix, 8, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        list_end = c->pin->sc.list_members;
+    }
     CK(cudaEventRecord(c->ev[4], c->stream));
     if (!hsegs.empty())
         CK(cudaMemcpyAsync(c->dsegs.p, hsegs.data(), hsegs.size() * sizeof(DevSegment), cudaMemcpyHostToDevice,
                            c->stream));
-    CK(cudaMemcpyAsync(c->work.p, c->cnt.p, (size_t)c->n * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (part) CK(cudaMemsetAsync(c->work.p, 0, (size_t)c->n * 4, c->stream));
+    else CK(cudaMemcpyAsync(c->work.p, c->cnt.p, (size_t)c->n * 4, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(c->picked.p, 0, (size_t)c->n, c->stream));
-    if (R) CK(cudaMemsetAsync(c->covered.p, 0, R, c->stream));
+    if (R) CK(cudaMemsetAsync(c->covered.p, 0, part ? prefix : R, c->stream));
+    if (part) CK(cudaMemsetAsync(P<uint8_t>(c->covered) + prefix, 1, R - prefix, c->stream));
     DBuf* zero_k[] = {&c->keys, &c->newly_n, &c->vol_cov, &c->vol_list, &c->bmp_cov, &c->ubmp_n};
     for (DBuf* z : zero_k) CK(cudaMemsetAsync(z->p, 0, (size_t)k * 8, c->stream));
 
@@ -870,6 +884,22 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out)
     s.force_mode = 0;
     if (const char* fm = std::getenv("IMM_SELECT_MODE"))
         s.force_mode = std::strcmp(fm, "decrement") == 0 ? 1 : std::strcmp(fm, "rebuild") == 0 ? 2 : 0;
+    if (part) {
+        s.list_members = list_end;
+        CK(launch_prefix_count(s, prefix, list_end, P<unsigned long long>(c->flags) + 1, c->di, c->stream));
+        c->acc_launches += 2 + (c->nbmp + 65534) / 65535;
+    }
+    return IMM_OK;
+}
+
+// Members of the stream's first `prefix` sets, as counted by the last
+// prefix selection's set-up (read after the stream has drained).
+int prefix_members(imm_ctx* c, uint64_t* out)
+{
+    CK(cudaMemcpyAsync(&c->pin->sc.list_members, P<unsigned long long>(c->flags) + 1, 8, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = c->pin->sc.list_members;
     return IMM_OK;
 }
 
@@ -1036,7 +1066,8 @@ struct Job {
     double lb = 1.0;
     uint32_t i = 1;
     int stage = 0;  // 0 sample round i, 1 select round i, 2 sample final, 3 select final, 4 done, 5 failed
-    uint64_t target = 0;
+    uint64_t target = 0;      // sets of the stream the next selection sees
+    uint64_t round_sets = 0;  // sets of the last estimation round's selection
     imm_stats st{};
     int status = IMM_OK;
     std::string err;
@@ -1057,7 +1088,7 @@ int job_final_target(Job& j)
     if (tf >= 4294967295.0) return set_err(j.w, IMM_EINVAL, "theta exceeds 2^32-2");
     j.st.lb = j.lb;
     j.st.theta = (uint64_t)tf;
-    j.target = std::max<uint64_t>(j.st.theta, j.w->nsets);
+    j.target = std::max<uint64_t>(j.st.theta, j.round_sets);
     j.stage = 2;
     return IMM_OK;
 }
@@ -1072,13 +1103,20 @@ int job_round_target(Job& j)
     return IMM_OK;
 }
 
-int job_start(Job& j)
+// keep_stream: a worker whose resident stream was drawn with the query's own
+// seed keeps it; the query's selections then see prefixes of it (sets are a
+// pure function of graph, seed and set id, so a prefix of the resident stream
+// is exactly the stream the query would sample).
+int job_start(Job& j, bool keep_stream = false)
 {
     imm_ctx* w = j.w;
     j.t0 = std::chrono::steady_clock::now();
-    drop_stream(w);
+    const bool keep = keep_stream && w->have_stream && w->seed == j.seed && w->nsets > 0;
+    if (!keep) drop_stream(w);
     reset_acc(w);
     std::memset(&j.st, 0, sizeof(j.st));
+    j.st.reused_sets = keep ? w->nsets : 0;
+    j.round_sets = 0;
     j.plan = theta_plan(w->n, j.k, j.eps, j.ell);
     j.st.lambda_prime = j.plan.lam_p;
     j.st.lambda_star = j.plan.lam_s;
@@ -1093,13 +1131,14 @@ int job_after_select(Job& j, uint64_t cov)
     imm_ctx* w = j.w;
     if (j.stage == 1) {
         const double x = std::ldexp(j.plan.nd, -(int)j.i);
-        const double nF = j.plan.nd * (double)cov / (double)w->nsets;
+        const double nF = j.plan.nd * (double)cov / (double)j.target;
         if (j.i - 1 < IMM_MAX_ROUNDS) {
             j.st.theta_i[j.i - 1] = j.target;
             j.st.covered_i[j.i - 1] = cov;
-            j.st.sets_i[j.i - 1] = w->nsets;
+            j.st.sets_i[j.i - 1] = j.target;
         }
         j.st.rounds = j.i;
+        j.round_sets = j.target;
         if (nF >= (1.0 + j.plan.eps_p) * x) {
             j.lb = nF / (1.0 + j.plan.eps_p);
             j.st.stopped_early = 1;
@@ -1113,9 +1152,10 @@ int job_after_select(Job& j, uint64_t cov)
     }
     // final selection
     std::memcpy(j.seeds_out, w->pin_seeds, (size_t)j.k * 4);
-    j.st.num_sets = w->nsets;
+    j.st.num_sets = j.target;
     j.st.covered = cov;
     j.st.members = w->nmembers;
+    if (j.target < w->nsets) TRY(prefix_members(w, &j.st.members));
     j.st.edges_examined = w->acc_edges;
     j.st.ms_sample = w->acc_sample_ms;
     j.st.ms_select = w->acc_select_ms;
@@ -1192,7 +1232,7 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     std::vector<SelectState> prep(L.size());
     std::vector<int> prc(L.size(), IMM_OK);
     for (size_t t = 0; t < L.size(); ++t) {
-        prc[t] = select_prepare(L[t]->w, L[t]->k, &prep[t]);
+        prc[t] = select_prepare(L[t]->w, L[t]->k, &prep[t], L[t]->target);
         if (prc[t] == IMM_OK) cudaEventRecord(L[t]->w->ev[4], L[t]->w->stream);
     }
     for (size_t t = 0; t < L.size(); ++t) {
@@ -1822,14 +1862,25 @@ void server_loop(imm_server* s)
                 auto& pool = s->idle[q->graph];
                 int rc = IMM_OK;
                 if (!pool.empty()) {
-                    w = pool.back();
-                    pool.pop_back();
+                    // with shared streams, an idle worker holding a stream
+                    // drawn with this query's seed is taken first
+                    size_t pick = pool.size() - 1;
+                    if (s->cfg.share_streams) {
+                        for (size_t i = 0; i < pool.size(); ++i) {
+                            if (pool[i]->have_stream && pool[i]->seed == q->job.seed && pool[i]->nsets > 0) {
+                                pick = i;
+                                break;
+                            }
+                        }
+                    }
+                    w = pool[pick];
+                    pool.erase(pool.begin() + (long)pick);
                 } else {
                     rc = make_worker(s->graphs[q->graph], &w, true);
                 }
                 q->job.w = w;
                 if (rc == IMM_OK && s->cfg.memory_budget_bytes) w->arena_limit = s->cfg.memory_budget_bytes / 2;
-                if (rc == IMM_OK) rc = job_start(q->job);
+                if (rc == IMM_OK) rc = job_start(q->job, s->cfg.share_streams != 0);
                 if (rc != IMM_OK) job_fail(q->job, rc);
                 s->active.push_back(q);
             }
@@ -1862,7 +1913,9 @@ void server_loop(imm_server* s)
             if (q->job.stage >= 4) {
                 q->finished = std::chrono::steady_clock::now();
                 if (q->job.w) {
-                    drop_stream(q->job.w);
+                    // shared streams: the idle worker keeps the query's stream
+                    // for a later query with the same seed
+                    if (!s->cfg.share_streams || q->job.stage != 4) drop_stream(q->job.w);
                     cudaStreamSynchronize(q->job.w->stream);
                     if (q->job.stage == 4 && s->idle[q->graph].size() < kServerIdlePerGraph)
                         s->idle[q->graph].push_back(q->job.w);

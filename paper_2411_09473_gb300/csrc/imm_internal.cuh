@@ -334,6 +334,10 @@ struct SelectState {
 };
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
                                 uint64_t* launches);
+// counts of the stream's first `prefix` sets into work (zero on entry);
+// list_end = off[prefix]; *members receives their total members
+cudaError_t launch_prefix_count(const SelectState& s, uint64_t prefix, uint64_t list_end,
+                                unsigned long long* members, const DeviceInfo& di, cudaStream_t st);
 // all k rounds in one cooperative launch over the whole GPU (one instance)
 cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st);
 // all k rounds of many instances in one launch, one CTA per instance

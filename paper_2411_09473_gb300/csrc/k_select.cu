@@ -640,6 +640,60 @@ select_cta_kernel(const SelectState* states, const uint32_t* ks, uint32_t count)
     }
 }
 
+// Counts of the first `prefix` sets of the stream (a selection over a prefix
+// of a longer resident stream sees only those sets): list-stored sets of ids
+// below the prefix occupy arena[0, off[prefix]); bitmap-stored ones are
+// those with bmp_set[b] < prefix, one block per (bitmap, chunk of words).
+// work must be zero on entry; *members receives the prefix's total members.
+__global__ void __launch_bounds__(256)
+prefix_list_count_kernel(const uint32_t* arena, uint64_t end, uint32_t* work, unsigned long long* members)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride)
+        atomicAdd(&work[arena[i]], 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(members, (unsigned long long)end);
+}
+
+__global__ void __launch_bounds__(256)
+prefix_bitmap_count_kernel(SelectState s, uint64_t prefix, unsigned long long* members)
+{
+    const uint32_t b = blockIdx.y;
+    if (b >= s.nbmp || s.bmp_set[b] >= prefix) return;
+    const uint32_t* row = s.bmp + (uint64_t)b * s.words;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < s.words; w += gridDim.x * blockDim.x) {
+        uint32_t x = row[w];
+        while (x) {
+            const int t = __ffs(x) - 1;
+            x &= x - 1;
+            atomicAdd(&s.work[w * 32 + t], 1u);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(members, (unsigned long long)s.bmp_len[b]);
+}
+
+cudaError_t launch_prefix_count(const SelectState& s, uint64_t prefix, uint64_t list_end,
+                                unsigned long long* members, const DeviceInfo& di, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(members, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (list_end + 255) / 256;
+    if (blocks > (uint64_t)di.sms * 8) blocks = (uint64_t)di.sms * 8;
+    if (blocks == 0) blocks = 1;
+    prefix_list_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.arena, list_end, s.work, members);
+    if (s.nbmp) {
+        const uint32_t bx = (s.words + 255 * 8) / (256 * 8) + 1;
+        for (uint32_t b0 = 0; b0 < s.nbmp; b0 += 65535) {
+            SelectState sc = s;
+            sc.bmp_set += b0;
+            sc.bmp += (uint64_t)b0 * s.words;
+            sc.bmp_len += b0;
+            sc.nbmp = s.nbmp - b0 < 65535 ? s.nbmp - b0 : 65535;
+            prefix_bitmap_count_kernel<<<dim3(bx, sc.nbmp), 256, 0, st>>>(sc, prefix, members);
+        }
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st)
 {
     int per_sm = 0;

@@ -51,6 +51,7 @@ class imm_stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_uint64),
         ("sample_edges", ctypes.c_uint64),
         ("sample_members", ctypes.c_uint64),
+        ("reused_sets", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -86,7 +87,8 @@ IMM_OPIM_KEY = 0xD1B54A32D192ED03
 
 
 class imm_server_config(ctypes.Structure):
-    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32)]
+    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32),
+                ("share_streams", ctypes.c_uint32)]
 
 
 class imm_completion(ctypes.Structure):
@@ -390,11 +392,13 @@ class _Server:
             pass
 
 
-def imm_server_create(graphs, memory_budget_bytes: int = 0, max_active: int = 64) -> _Server:
-    """Continuous-batching server over loaded graph contexts (kept alive by the handle)."""
+def imm_server_create(graphs, memory_budget_bytes: int = 0, max_active: int = 64,
+                      share_streams: bool = False) -> _Server:
+    """Continuous-batching server over loaded graph contexts (kept alive by the
+    handle); share_streams: prefix-stable reuse of resident streams."""
     arr = (ctypes.c_void_p * len(graphs))(*[g.handle.value if hasattr(g.handle, "value") else g.handle
                                               for g in graphs])
-    cfg = imm_server_config(memory_budget_bytes, max_active)
+    cfg = imm_server_config(memory_budget_bytes, max_active, 1 if share_streams else 0)
     h = ctypes.c_void_p()
     rc = _load().imm_server_create(ctypes.byref(h), arr, len(graphs), ctypes.byref(cfg))
     if rc != IMM_OK:

@@ -135,3 +135,40 @@ def test_served_stream_equals_oracle_runs(imm):
         assert_run_equals_golden(seeds, st, rec, f"query {j}")
     for c in ctxs:
         imm.imm_destroy(c)
+
+
+def test_served_shared_streams_equal_oracle_runs(imm):
+    """Prefix-stable stream sharing: queries on the same graph with the same
+    rng seed (and different k and epsilon) reuse the resident stream of the
+    previous one, and each still equals the oracle's run of it alone."""
+    from gpu_common import oracle_for
+    graphs = [graphgen.make_graph(4096, 32768, 1, graphgen.IC, "inv_indeg"),
+              graphgen.make_graph(6000, 60000, 2, graphgen.LT, "inv_indeg")]
+    ctxs = [load(imm, g) for g in graphs]
+    srv = imm.imm_server_create(ctxs, memory_budget_bytes=8 << 30, max_active=4, share_streams=True)
+    # (graph, k, eps, seed, reuses): one query at a time, so each graph has one
+    # idle worker; a query with that worker's seed reuses its stream, one with
+    # another seed replaces it
+    plan = [(0, 10, 0.5, 11, False), (0, 5, 0.3, 11, True), (0, 20, 0.45, 11, True), (0, 10, 0.5, 12, False),
+            (0, 10, 0.5, 11, False), (1, 25, 0.4, 13, False), (1, 10, 0.2, 13, True), (1, 40, 0.5, 13, True)]
+    for (gid, k, eps, seed, reuses) in plan:
+        qid = imm.imm_server_submit(srv, gid, k, eps, 1.0, seed)
+        got = None
+        deadline = time.time() + 120
+        while got is None and time.time() < deadline:
+            for (cid, status, _, _) in imm.imm_server_poll(srv):
+                assert cid == qid and status == 0
+                got = imm.imm_server_take(srv, qid, k)
+            time.sleep(0.002)
+        assert got is not None
+        seeds, st = got
+        g = graphs[gid]
+        o = oracle_for(g)
+        want, ost = o.run(k, eps, 1.0, seed)
+        assert np.array_equal(seeds, want), (gid, k, eps, seed)
+        assert st.rounds == ost.rounds and st.theta == ost.theta and st.lb == ost.lb
+        assert st.num_sets == ost.num_sets and st.covered == ost.covered and st.members == o.num_members
+        for i in range(st.rounds):
+            assert st.covered_i[i] == ost.covered_i[i] and st.sets_i[i] == ost.sets_i[i]
+        assert (st.reused_sets > 0) == reuses, (gid, k, eps, seed, st.reused_sets)
+    imm.imm_server_destroy(srv)
