@@ -100,6 +100,7 @@ struct imm_ctx {
 
     // selection scratch
     DBuf work, picked, covered, newly, keys, newly_n, vol_cov, vol_list, bmp_cov, ubmp, ubmp_n, seeds, dsegs, dstate;
+    DBuf cand, cstate;
 
     DBuf flags;
     uint64_t arena_limit = 0;
@@ -129,6 +130,8 @@ struct imm_ctx {
     uint32_t* pin_seeds = nullptr;
     unsigned long long* pin_newly = nullptr;
     uint32_t pin_k = 0;
+    void* pin_stage = nullptr;  // batch engine: selection states staged for the device
+    size_t pin_stage_bytes = 0;
 };
 
 namespace {
@@ -289,6 +292,7 @@ void free_graph(imm_ctx* c)
     dfree(c, c->vtmp);
     dfree(c, c->work);
     dfree(c, c->picked);
+    dfree(c, c->cand);
     dfree(c, c->slot_q);
     dfree(c, c->slot_bm);
     dfree(c, c->grp);
@@ -828,6 +832,8 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     TRY(ensure(c, c->ubmp, std::max<uint64_t>(c->nbmp, 1) * 4));
     TRY(ensure(c, c->ubmp_n, (size_t)k * 8));
     TRY(ensure(c, c->seeds, (size_t)k * 4));
+    TRY(ensure(c, c->cand, (size_t)c->n * 4));
+    TRY(ensure(c, c->cstate, 16));
     std::vector<DevSegment> hsegs;
     for (auto& sg : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(sg.voff), P<uint32_t>(sg.inv)});
     TRY(ensure(c, c->dsegs, std::max<size_t>(hsegs.size(), 1) * sizeof(DevSegment)));
@@ -851,6 +857,7 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     if (part) CK(cudaMemsetAsync(P<uint8_t>(c->covered) + prefix, 1, R - prefix, c->stream));
     DBuf* zero_k[] = {&c->keys, &c->newly_n, &c->vol_cov, &c->vol_list, &c->bmp_cov, &c->ubmp_n};
     for (DBuf* z : zero_k) CK(cudaMemsetAsync(z->p, 0, (size_t)k * 8, c->stream));
+    CK(cudaMemsetAsync(c->cstate.p, 0, 16, c->stream));
 
     SelectState& s = *out;
     s.n = c->n;
@@ -879,6 +886,11 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
+    // IMM_SELECT_CAND=0 (tests): every argmax scans all n vertices
+    const char* cf = std::getenv("IMM_SELECT_CAND");
+    const bool cand = !(cf && std::strcmp(cf, "0") == 0);
+    s.cand = cand ? P<uint32_t>(c->cand) : nullptr;
+    s.cstate = P<uint32_t>(c->cstate);
     // IMM_SELECT_MODE=decrement|rebuild (tests): one counter update for every
     // round; the two give the same counts (Sec. IV-C), which the tests check
     s.force_mode = 0;
@@ -907,14 +919,17 @@ int prefix_members(imm_ctx* c, uint64_t* out)
 int select_readback(imm_ctx* c, uint32_t k, cudaStream_t st)
 {
     if (c->pin_k < k) {
+        // grown geometrically: freeing pinned memory synchronises the whole
+        // device, which would stall every other stream of a batch or server
+        const uint32_t cap = std::max<uint32_t>(k, std::max<uint32_t>(256u, c->pin_k * 2u));
         if (c->pin_seeds) cudaFreeHost(c->pin_seeds);
         if (c->pin_newly) cudaFreeHost(c->pin_newly);
         c->pin_seeds = nullptr;
         c->pin_newly = nullptr;
         c->pin_k = 0;
-        CK(cudaMallocHost(&c->pin_seeds, (size_t)k * 4));
-        CK(cudaMallocHost(&c->pin_newly, (size_t)k * 8));
-        c->pin_k = k;
+        CK(cudaMallocHost(&c->pin_seeds, (size_t)cap * 4));
+        CK(cudaMallocHost(&c->pin_newly, (size_t)cap * 8));
+        c->pin_k = cap;
     }
     CK(cudaMemcpyAsync(c->pin_seeds, c->seeds.p, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(c->pin_newly, c->newly_n.p, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
@@ -947,6 +962,10 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
         CK(launch_select_batch(P<SelectState>(c->dstate), dk, 1, c->di, c->stream));
         c->acc_launches += 1;
     } else {
+        // the whole-grid rounds are bound by their grid barriers, not by the
+        // argmax scan, so they scan every vertex (no candidate list, which
+        // costs barriers of its own)
+        s.cand = nullptr;
         const cudaError_t ce =
             coop_launch(c->device, c->stream, [&] { return launch_select_all(s, k, c->di, c->stream); });
         if (ce == cudaErrorCooperativeLaunchTooLarge || ce == cudaErrorNotSupported) {
@@ -1183,7 +1202,39 @@ double ms_since(std::chrono::steady_clock::time_point t)
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
 }
 
-int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64_t* launches)
+// The selection launched by one wave runs while the next wave samples the
+// other queries; that wave collects it (waiting only if it is still running)
+// before it launches its own.  The jobs of an in-flight selection neither
+// sample nor select until collected.
+struct WaveState {
+    std::vector<Job*> inflight;
+    cudaEvent_t done = nullptr;  // recorded on the master stream after the selection's read-backs
+    ~WaveState()
+    {
+        if (done) cudaEventDestroy(done);
+    }
+};
+
+int collect_selection(WaveState& ws, imm_ctx* host)
+{
+    if (ws.inflight.empty()) return IMM_OK;
+    std::vector<Job*> L;
+    L.swap(ws.inflight);
+    const cudaError_t e = cudaEventSynchronize(ws.done);
+    if (e != cudaSuccess) {
+        for (Job* j : L) job_fail(*j, IMM_ECUDA);
+        return cuda_err(host, e, "batched selection");
+    }
+    for (Job* j : L) {
+        const uint64_t cov = select_covered(j->w, j->k, nullptr);
+        int rc = job_after_select(*j, cov);
+        if (rc == IMM_OK && (j->stage == 0 || j->stage == 2)) rc = begin_stream(j->w, j->target, j->seed);
+        if (rc != IMM_OK) job_fail(*j, rc);
+    }
+    return IMM_OK;
+}
+
+int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64_t* launches, WaveState& ws)
 {
     std::vector<Job*> S;
     for (Job* j : jobs) {
@@ -1216,11 +1267,18 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         else if (j->w->nsets >= j->target) ++j->stage;
     }
     const double t_sample = ms_since(tw0);
+    // the previous wave's selection has run beside these phases
+    const auto tc0 = std::chrono::steady_clock::now();
+    const size_t collected = ws.inflight.size();
+    TRY(collect_selection(ws, host));
+    const double t_collect = ms_since(tc0);
     std::vector<Job*> L;
     for (Job* j : jobs)
         if (j->stage == 1 || j->stage == 3) L.push_back(j);
     if (L.empty()) {
-        if (trace_on()) fprintf(stderr, "imm wave: sample %zu jobs %.2f ms\n", S.size(), t_sample);
+        if (trace_on())
+            fprintf(stderr, "imm wave: sample %zu jobs %.2f ms | collect %zu %.2f ms\n", S.size(), t_sample,
+                    collected, t_collect);
         return IMM_OK;
     }
     const auto tp0 = std::chrono::steady_clock::now();
@@ -1249,12 +1307,26 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     if (ok.empty()) return IMM_OK;
     const size_t nbytes = ok.size() * (rec + 4) + 16;
     TRY(ensure(host, host->bstates, nbytes));
-    // the states are staged through pinned memory owned by the engine call
-    void* hbuf = nullptr;
-    if (cudaMallocHost(&hbuf, nbytes) != cudaSuccess) {
-        cudaGetLastError();
-        return set_err(host, IMM_ECUDA, "pinned staging allocation failed");
+    // the states are staged through pinned memory the host context keeps
+    // (grown geometrically: freeing pinned memory synchronises the device);
+    // the previous selection has been collected, so both are free
+    if (host->pin_stage_bytes < nbytes) {
+        const size_t cap = std::max(nbytes, host->pin_stage_bytes * 2);
+        if (host->pin_stage) cudaFreeHost(host->pin_stage);
+        host->pin_stage = nullptr;
+        host->pin_stage_bytes = 0;
+        if (cudaMallocHost(&host->pin_stage, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(host, IMM_ECUDA, "pinned staging allocation failed");
+        }
+        host->pin_stage_bytes = cap;
     }
+    if (!ws.done && cudaEventCreateWithFlags(&ws.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ws.done = nullptr;
+        return set_err(host, IMM_ECUDA, "event creation failed");
+    }
+    void* hbuf = host->pin_stage;
     std::memcpy(hbuf, states.data(), ok.size() * rec);
     std::memcpy(static_cast<char*>(hbuf) + ok.size() * rec, ks.data(), ok.size() * 4);
     cudaError_t e = cudaMemcpyAsync(host->bstates.p, hbuf, ok.size() * (rec + 4), cudaMemcpyHostToDevice, master);
@@ -1268,25 +1340,22 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         j->w->acc_launches += 1;
         if (select_readback(j->w, j->k, master) != IMM_OK) e = cudaErrorUnknown;
     }
-    const double t_prep = ms_since(tp0);
-    const auto ts0 = std::chrono::steady_clock::now();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(master);
+    if (e == cudaSuccess) e = cudaEventRecord(ws.done, master);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(master);
+        for (Job* j : ok) job_fail(*j, IMM_ECUDA);
+        return cuda_err(host, e, "batched selection");
+    }
+    ws.inflight = ok;
     if (trace_on()) {
         uint32_t kmax = 0, nmax = 0;
         for (Job* j : ok) {
             kmax = std::max(kmax, j->k);
             nmax = std::max(nmax, j->w->n);
         }
-        fprintf(stderr, "imm wave: sample %zu jobs %.2f ms | select %zu jobs: prepare %.2f ms, kernel+sync %.2f ms "
-                        "(k<=%u, n<=%u)\n", S.size(), t_sample, ok.size(), t_prep, ms_since(ts0), kmax, nmax);
-    }
-    cudaFreeHost(hbuf);
-    if (e != cudaSuccess) return cuda_err(host, e, "batched selection");
-    for (Job* j : ok) {
-        const uint64_t cov = select_covered(j->w, j->k, nullptr);
-        int rc = job_after_select(*j, cov);
-        if (rc == IMM_OK && (j->stage == 0 || j->stage == 2)) rc = begin_stream(j->w, j->target, j->seed);
-        if (rc != IMM_OK) job_fail(*j, rc);
+        fprintf(stderr, "imm wave: sample %zu jobs %.2f ms | collect %zu %.2f ms | select %zu jobs: launch %.2f ms "
+                        "(k<=%u, n<=%u)\n", S.size(), t_sample, collected, t_collect, ok.size(), ms_since(tp0), kmax,
+                nmax);
     }
     return IMM_OK;
 }
@@ -1348,7 +1417,7 @@ void imm_destroy(imm_ctx* c)
                     &c->covered,  &c->newly,   &c->keys,     &c->newly_n, &c->vol_cov,   &c->vol_list,
                     &c->bmp_cov,  &c->ubmp,    &c->ubmp_n,   &c->seeds,   &c->dsegs,     &c->flags,
                     &c->set_bmp,  &c->bmp,     &c->dstate,
-                    &c->bmp_set,  &c->bmp_len};
+                    &c->bmp_set,  &c->bmp_len, &c->cand,     &c->cstate};
     for (DBuf* b : bufs) dfree(c, *b);
     cudaStreamSynchronize(c->stream);
     for (auto& e : c->ev)
@@ -1356,6 +1425,7 @@ void imm_destroy(imm_ctx* c)
     if (c->pin) cudaFreeHost(c->pin);
     if (c->pin_seeds) cudaFreeHost(c->pin_seeds);
     if (c->pin_newly) cudaFreeHost(c->pin_newly);
+    if (c->pin_stage) cudaFreeHost(c->pin_stage);
     delete c;
 }
 
@@ -1769,11 +1839,16 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
         rc = IMM_OK;
     }
     uint64_t launches = 0;
-    while (rc == IMM_OK) {
-        bool any = false;
-        for (Job* j : active) any = any || (j->stage < 4);
-        if (!any) break;
-        rc = run_wave(active, g0, g0->stream, &launches);
+    {
+        WaveState ws;
+        while (rc == IMM_OK) {
+            bool any = false;
+            for (Job* j : active) any = any || (j->stage < 4);
+            if (!any) break;
+            rc = run_wave(active, g0, g0->stream, &launches, ws);
+        }
+        // nothing may still run on the workers' buffers when they are freed
+        cudaStreamSynchronize(g0->stream);
     }
     for (uint32_t q = 0; q < nq; ++q) {
         if (status_out) status_out[q] = jobs[q].stage == 4 ? IMM_OK : (jobs[q].status ? jobs[q].status : rc);
@@ -1823,6 +1898,7 @@ struct imm_server {
     uint64_t waves = 0, launches = 0;
     int fatal = IMM_OK;
     std::string err;
+    WaveState wave;  // the selection in flight between waves
 };
 
 namespace {
@@ -1888,10 +1964,13 @@ void server_loop(imm_server* s)
         if (s->active.empty()) continue;
         std::vector<Job*> jobs;
         for (ServedQuery* q : s->active) jobs.push_back(&q->job);
-        const int rc = run_wave(jobs, s->host, s->host->stream, &s->launches);
+        const int rc = run_wave(jobs, s->host, s->host->stream, &s->launches, s->wave);
         ++s->waves;
         std::lock_guard<std::mutex> lk(s->mu);
         if (rc != IMM_OK) {
+            // no selection may still run on a worker that is freed below
+            cudaStreamSynchronize(s->host->stream);
+            s->wave.inflight.clear();
             // the loop stops: every query in flight or still queued completes
             // with the error, so no client waits forever
             s->fatal = rc;
@@ -2051,6 +2130,7 @@ void imm_server_destroy(imm_server* s)
     s->cv.notify_one();
     if (s->loop.joinable()) s->loop.join();
     DeviceGuard guard(s->host->device);
+    cudaStreamSynchronize(s->host->stream);  // a selection may still be in flight
     for (ServedQuery* q : s->active) {
         destroy_worker(q->job.w);
         delete q;

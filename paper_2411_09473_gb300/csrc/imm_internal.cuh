@@ -331,6 +331,8 @@ struct SelectState {
     const DevSegment* segs;
     uint32_t nsegs;
     int force_mode;      // 0: decrement or recount chosen per round; 1: always decrement; 2: always recount
+    uint32_t* cand;      // n (nullable): argmax candidates, the unpicked vertices with counts >= tau
+    uint32_t* cstate;    // 4: candidates, tau, list valid, count of the last list that came out too long
 };
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
                                 uint64_t* launches);

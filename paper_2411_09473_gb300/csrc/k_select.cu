@@ -345,6 +345,63 @@ __device__ void team_argmax(const SelectState& s, uint32_t j, Team t, unsigned l
     }
 }
 
+// Argmax over the candidate list (same key and reduction as team_argmax).
+// Counts never increase during a selection, so when every vertex left off
+// the list held fewer than tau occurrences at the time it was built, the
+// list's best key is the global one whenever its count is at least tau:
+// every vertex holding that count is on the list, so the lowest id among
+// them is the lowest overall.
+template <class Team>
+__device__ void team_argmax_cand(const SelectState& s, uint32_t j, Team t, unsigned long long* s_red)
+{
+    unsigned long long best = 0;
+    const uint32_t nc = __ldcg(s.cstate);
+    for (uint64_t i = t.rank(); i < nc; i += t.size()) {
+        const uint32_t v = s.cand[i];
+        if (!s.picked[v]) {
+            const unsigned long long key = ((unsigned long long)s.work[v] << 32) | (0xFFFFFFFFu - v);
+            best = key > best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+        best = o > best ? o : best;
+    }
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 0) s_red[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+        best = lane < nwarps ? s_red[lane] : 0ull;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+            best = o > best ? o : best;
+        }
+        if (lane == 0 && best) atomicMax(&s.keys[j], best);
+    }
+    __syncthreads();  // s_red is reused by the next reduction
+}
+
+// The candidate list: unpicked vertices with counts >= tau (one append
+// atomic per warp).
+template <class Team>
+__device__ void team_build_cand(const SelectState& s, uint32_t tau, Team t)
+{
+    const uint64_t lane = threadIdx.x & 31;
+    for (uint64_t v0 = t.rank() - lane; v0 < s.n; v0 += t.size()) {
+        const uint64_t v = v0 + lane;
+        const bool take = v < s.n && !s.picked[v] && s.work[v] >= tau;
+        const uint32_t bal = __ballot_sync(kFull, take);
+        if (!bal) continue;
+        const int leader = __ffs(bal) - 1;
+        uint32_t base = 0;
+        if ((int)lane == leader) base = atomicAdd(s.cstate, (uint32_t)__popc(bal));
+        base = __shfl_sync(kFull, base, leader);
+        if (take) s.cand[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)v;
+    }
+}
+
 // Appends the set ids of a warp's `take` lanes to the round's newly covered
 // list with one atomic per warp (the list's counter is a single address).
 __device__ __forceinline__ void append_newly(const SelectState& s, uint32_t j, bool take, uint32_t sid)
@@ -593,12 +650,55 @@ __device__ void team_count_uncovered(const SelectState& s, uint32_t j, Team t)
     }
 }
 
+// The argmax of a round scans the candidate list when one is valid and its
+// best count reaches tau; otherwise all n vertices, and the list is rebuilt
+// with tau = a quarter of that round's best count.  A list longer than n/8
+// is dropped (scanning it would cost about as much as the full pass), and no
+// new one is built until the best count has halved since.  The picks are
+// those of the full scan in every round.
+template <class Team>
+__device__ void team_pick(const SelectState& s, uint32_t j, Team t, unsigned long long* s_red)
+{
+    if (s.cand && __ldcg(s.cstate + 2)) {
+        team_argmax_cand(s, j, t, s_red);
+        t.sync();
+        const unsigned long long key = __ldcg(&s.keys[j]);
+        if (key != 0ull && (uint32_t)(key >> 32) >= __ldcg(s.cstate + 1)) return;
+        t.sync();  // every thread has read the key before it is reset
+        if (t.rank() == 0) {
+            s.keys[j] = 0ull;
+            s.cstate[2] = 0u;
+        }
+        t.sync();
+    }
+    team_argmax(s, j, t, s_red);
+    t.sync();
+    if (!s.cand) return;
+    const uint32_t best = (uint32_t)(__ldcg(&s.keys[j]) >> 32);
+    const uint32_t last_long = __ldcg(s.cstate + 3);
+    if (best == 0u || (last_long && best > last_long / 2)) return;
+    const uint32_t tau = best >> 2 ? best >> 2 : 1u;
+    if (t.rank() == 0) {
+        s.cstate[0] = 0u;
+        s.cstate[1] = tau;
+    }
+    t.sync();
+    team_build_cand(s, tau, t);
+    t.sync();
+    if (t.rank() == 0) {
+        const uint32_t nc = s.cstate[0];
+        const bool keep = (uint64_t)nc * 8 <= s.n;
+        s.cstate[2] = keep ? 1u : 0u;
+        s.cstate[3] = keep ? 0u : best;
+    }
+    t.sync();
+}
+
 template <class Team>
 __device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_mode, unsigned long long* s_red)
 {
     for (uint32_t j = 0; j < k; ++j) {
-        team_argmax(s, j, t, s_red);
-        t.sync();
+        team_pick(s, j, t, s_red);
         if (s.nbmp == 0 && s.force_mode != 2) {
             team_cover_decrement(s, j, t);
             t.sync();
