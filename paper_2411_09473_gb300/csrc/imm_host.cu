@@ -1206,6 +1206,18 @@ double ms_since(std::chrono::steady_clock::time_point t)
 // other queries; that wave collects it (waiting only if it is still running)
 // before it launches its own.  The jobs of an in-flight selection neither
 // sample nor select until collected.
+// Instances on graphs of at least this many vertices select with a cluster
+// of CTAs (IMM_SELECT_CLUSTER_MIN_N overrides it; tests use 0 to send every
+// instance there, and a value above every n keeps one CTA per instance).
+uint32_t select_cluster_min_n()
+{
+    static const uint32_t v = [] {
+        const char* e = std::getenv("IMM_SELECT_CLUSTER_MIN_N");
+        return e ? (uint32_t)std::strtoul(e, nullptr, 10) : (1u << 15);
+    }();
+    return v;
+}
+
 struct WaveState {
     std::vector<Job*> inflight;
     cudaEvent_t done = nullptr;  // recorded on the master stream after the selection's read-backs
@@ -1293,18 +1305,26 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         prc[t] = select_prepare(L[t]->w, L[t]->k, &prep[t], L[t]->target);
         if (prc[t] == IMM_OK) cudaEventRecord(L[t]->w->ev[4], L[t]->w->stream);
     }
-    for (size_t t = 0; t < L.size(); ++t) {
-        Job* j = L[t];
-        if (prc[t] != IMM_OK) {
-            job_fail(*j, prc[t]);
-            continue;
+    // instances on graphs of >= cluster_min_n vertices select with a cluster
+    // of CTAs each, the others with one CTA; the small ones come first
+    const uint32_t cluster_min_n = select_cluster_min_n();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (size_t t = 0; t < L.size(); ++t) {
+            Job* j = L[t];
+            if (prc[t] != IMM_OK) {
+                if (pass == 0) job_fail(*j, prc[t]);
+                continue;
+            }
+            if ((j->w->n >= cluster_min_n) != (pass == 1)) continue;
+            states[ok.size()] = prep[t];
+            ks[ok.size()] = j->k;
+            cudaStreamWaitEvent(master, j->w->ev[4], 0);
+            ok.push_back(j);
         }
-        states[ok.size()] = prep[t];
-        ks[ok.size()] = j->k;
-        cudaStreamWaitEvent(master, j->w->ev[4], 0);
-        ok.push_back(j);
     }
     if (ok.empty()) return IMM_OK;
+    uint32_t nsmall = 0;
+    while (nsmall < ok.size() && ok[nsmall]->w->n < cluster_min_n) ++nsmall;
     const size_t nbytes = ok.size() * (rec + 4) + 16;
     TRY(ensure(host, host->bstates, nbytes));
     // the states are staged through pinned memory the host context keeps
@@ -1330,11 +1350,18 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     std::memcpy(hbuf, states.data(), ok.size() * rec);
     std::memcpy(static_cast<char*>(hbuf) + ok.size() * rec, ks.data(), ok.size() * 4);
     cudaError_t e = cudaMemcpyAsync(host->bstates.p, hbuf, ok.size() * (rec + 4), cudaMemcpyHostToDevice, master);
-    if (e == cudaSuccess)
-        e = launch_select_batch(P<SelectState>(host->bstates),
-                                reinterpret_cast<const uint32_t*>(static_cast<char*>(host->bstates.p) + ok.size() * rec),
-                                (uint32_t)ok.size(), host->di, master);
-    if (launches) *launches += 1;
+    const SelectState* dst = P<SelectState>(host->bstates);
+    const uint32_t* dks = reinterpret_cast<const uint32_t*>(static_cast<char*>(host->bstates.p) + ok.size() * rec);
+    const uint32_t nbig = (uint32_t)ok.size() - nsmall;
+    if (e == cudaSuccess && nsmall) e = launch_select_batch(dst, dks, nsmall, host->di, master);
+    if (e == cudaSuccess && nbig) {
+        e = launch_select_clusters(dst + nsmall, dks + nsmall, nbig, host->di, master);
+        if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+            cudaGetLastError();
+            e = launch_select_batch(dst + nsmall, dks + nsmall, nbig, host->di, master);
+        }
+    }
+    if (launches) *launches += (nsmall ? 1 : 0) + (nbig ? 1 : 0);
     for (Job* j : ok) {
         if (e != cudaSuccess) break;
         j->w->acc_launches += 1;

@@ -342,6 +342,12 @@ cudaError_t launch_prefix_count(const SelectState& s, uint64_t prefix, uint64_t 
                                 unsigned long long* members, const DeviceInfo& di, cudaStream_t st);
 // all k rounds in one cooperative launch over the whole GPU (one instance)
 cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st);
+// all k rounds of many instances in one launch, one cluster of kClusterSel
+// CTAs per instance (states and ks in device memory); cudaErrorCooperative-
+// LaunchTooLarge if no cluster of that size fits the device
+constexpr uint32_t kClusterSel = 8;
+cudaError_t launch_select_clusters(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,
+                                   const DeviceInfo& di, cudaStream_t st);
 // all k rounds of many instances in one launch, one CTA per instance
 // (states and ks in device memory)
 cudaError_t launch_select_batch(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,

@@ -296,6 +296,18 @@ struct BlockTeam {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// A thread-block cluster (kClusterSel CTAs on as many SMs of one GPC) as the
+// team of one instance: its barrier is the cluster's, with release/acquire
+// semantics at cluster scope, far cheaper than a grid barrier.
+struct ClusterTeam {
+    __device__ __forceinline__ uint64_t rank() const
+    {
+        return (uint64_t)cg::this_cluster().block_rank() * blockDim.x + threadIdx.x;
+    }
+    __device__ __forceinline__ uint64_t size() const { return (uint64_t)cg::this_cluster().num_blocks() * blockDim.x; }
+    __device__ __forceinline__ void sync() const { cg::this_cluster().sync(); }
+};
+
 // s_red: one slot per warp of the block; the block's best key goes to the
 // round's key with one atomic (not one per warp: they all hit one address).
 template <class Team>
@@ -792,6 +804,46 @@ cudaError_t launch_prefix_count(const SelectState& s, uint64_t prefix, uint64_t 
         }
     }
     return cudaGetLastError();
+}
+
+// All k rounds of many instances in one launch, one cluster per instance.
+__global__ void __launch_bounds__(512, 1)
+select_cluster_kernel(const SelectState* states, const uint32_t* ks, uint32_t count)
+{
+    __shared__ int s_mode;
+    __shared__ unsigned long long s_red[32];
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t nb = cl.num_blocks();
+    const uint32_t cid = blockIdx.x / nb, ncl = gridDim.x / nb;
+    for (uint32_t i = cid; i < count; i += ncl) {
+        select_rounds(states[i], ks[i], ClusterTeam{}, &s_mode, s_red);
+        cl.sync();
+    }
+}
+
+cudaError_t launch_select_clusters(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,
+                                   const DeviceInfo& di, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterSel;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(kClusterSel);
+    int fit = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&fit, select_cluster_kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (fit < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const uint32_t ncl = count < (uint32_t)fit ? count : (uint32_t)fit;
+    cfg.gridDim = dim3(ncl * kClusterSel);
+    return cudaLaunchKernelEx(&cfg, select_cluster_kernel, d_states, d_ks, count);
 }
 
 cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st)

@@ -93,3 +93,45 @@ def test_batch64_equals_oracle_runs(imm):
         assert_run_equals_golden(seeds[i], stats[i], rec, f"instance {i}")
     for c in ctxs:
         imm.imm_destroy(c)
+
+
+_FORCED = r"""
+import sys
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import numpy as np
+import graphgen
+from gpu_common import oracle_for
+from paper_2411_09473_gb300 import imm
+b = graphgen.batch_workload(count=12, max_log_n=14.0)
+ctxs = []
+for g in b.graphs:
+    c = imm.imm_create(device=0)
+    imm.imm_load_graph(c, g.n, g.m, g.row, g.src, g.weight, g.model)
+    ctxs.append(c)
+seeds, stats, status = imm.imm_run_batch([(ctxs[q.graph_id], q.k, q.epsilon, q.ell, q.seed) for q in b.queries])
+assert status == [0] * len(b.queries), status
+for i, q in enumerate(b.queries):
+    g = b.graphs[q.graph_id]
+    o = oracle_for(g)
+    want, ost = o.run(q.k, q.epsilon, q.ell, q.seed)
+    assert np.array_equal(seeds[i], want), i
+    st = stats[i]
+    assert st.theta == ost.theta and st.covered == ost.covered and st.lb == ost.lb and st.num_sets == ost.num_sets
+print("forced ok")
+"""
+
+
+@pytest.mark.parametrize("min_n", ["0", "4294967295"])
+def test_batch_selection_teams_forced(min_n):
+    """Every instance selects with a cluster of CTAs (min_n = 0), or every one
+    with a single CTA: both equal the oracle's runs (a fresh process, since
+    the threshold is read once)."""
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = _FORCED.format(root=os.path.dirname(here), tests=here)
+    env = dict(os.environ, IMM_SELECT_CLUSTER_MIN_N=min_n)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "forced ok" in r.stdout, r.stderr[-3000:]
