@@ -13,7 +13,9 @@
  *     during the call; the library never keeps them.
  *   - Device memory is library-owned.  It comes from the optional allocator
  *     given to imm_create (e.g. PyTorch's caching allocator), otherwise from
- *     cudaMallocAsync on the context's stream.
+ *     stream-ordered allocations (cudaMallocFromPoolAsync on the context's
+ *     stream) in a memory pool the library keeps per device; that pool
+ *     retains freed memory for reuse until the process exits.
  *   - All GPU work of a context is issued on the stream given to imm_create
  *     (NULL = the legacy default stream).  Calls that return host results
  *     synchronise that stream before returning.
@@ -90,7 +92,7 @@ typedef struct imm_stats {
 } imm_stats;
 
 /* Create a context on CUDA device `device`.  `alloc` may be NULL (then
- * cudaMallocAsync is used); `stream` is a cudaStream_t or NULL.
+ * the library's memory pool is used); `stream` is a cudaStream_t or NULL.
  * Errors: EINVAL (out==NULL or bad device), ECUDA. */
 int imm_create(imm_ctx** out, int device, const imm_alloc* alloc, void* stream);
 
@@ -236,7 +238,11 @@ typedef struct imm_query {
  * inputs.  seeds_out (host) receives the queries' seeds concatenated in query
  * order (sum of k entries); stats_out (host, nq entries, nullable) and
  * status_out (host, nq entries, nullable) receive per-query statistics and
- * status.  The graph contexts' RRR-set streams are not touched.
+ * status.  The graph contexts' RRR-set streams are not touched.  The
+ * queries' own buffers come from their graph context's allocator (the
+ * library's memory pool if it has none), on the queries' own streams, and
+ * selections of instances on graphs of >= 2^15 vertices run on thread-block
+ * clusters.
  * Errors: EINVAL (a query's graph missing or not loaded, contexts on
  * different devices, bad k/epsilon/ell); a query that fails on its own
  * (ENOMEM under the graph context's arena limit, ...) reports its status in
@@ -252,7 +258,7 @@ int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* seeds_out, im
  * memory_budget_bytes (0 = no limit; each query's arena is then limited to
  * half the budget), so queries that arrive while others are on the GPU join
  * the next wave and overlap with them.  Every result equals the query's solo
- * imm_run.  Server workers allocate with cudaMallocAsync on their own
+ * imm_run.  Server workers allocate from the library's memory pool on their own
  * streams (never through the contexts' allocator callbacks). */
 typedef struct imm_server imm_server;
 

@@ -189,6 +189,41 @@ void dfree(imm_ctx* c, DBuf& b)
     b = DBuf{};
 }
 
+// The library's own stream-ordered memory pool of a device (contexts without
+// an allocator, and batch and server workers, allocate from it).  Freed
+// memory stays in the pool for the next allocation instead of going back to
+// the driver at every synchronisation, as a caching allocator would keep it;
+// the pool lives until the process exits.  Null if the device has none.
+cudaMemPool_t lib_pool(int device)
+{
+    static std::mutex mu;
+    static std::unordered_map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        uint64_t keep = ~0ull;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+        // memory freed on one worker's stream is not handed to another
+        // worker's stream by making that stream wait for the first: batch and
+        // server workers must not serialise on each other
+        int no = 0;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess)
+            cudaGetLastError();
+    }
+    pools[device] = pool;
+    return pool;
+}
+
 int dalloc(imm_ctx* c, DBuf& b, size_t bytes)
 {
     dfree(c, b);
@@ -197,9 +232,14 @@ int dalloc(imm_ctx* c, DBuf& b, size_t bytes)
     void* p = nullptr;
     if (c->has_alloc) {
         p = c->alloc.alloc(c->alloc.user, bytes, c->stream);
-    } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
-        cudaGetLastError();
-        p = nullptr;
+    } else {
+        cudaMemPool_t pool = lib_pool(c->device);
+        const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, c->stream)
+                                   : cudaMallocAsync(&p, bytes, c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
     }
     if (!p) return set_err(c, IMM_ENOMEM, "device allocation of %zu bytes failed", bytes);
     b.p = p;
@@ -1260,25 +1300,36 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     // phase-major: every job's launches are issued before any stream is
     // drained, so the jobs' kernels overlap on the GPU
     const auto tw0 = std::chrono::steady_clock::now();
+    double t_sync = 0.0, t_p[3] = {0.0, 0.0, 0.0};
     for (Job* j : S) {
         const int rc = batch_phase1(j->w, j->target);
         if (rc != IMM_OK) job_fail(*j, rc);
     }
+    t_p[0] = ms_since(tw0);
     for (Job* j : S) {
         if (j->stage == 5) continue;
+        const auto ta = std::chrono::steady_clock::now();
         int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+        t_sync += ms_since(ta);
         if (rc == IMM_OK) rc = batch_phase2(j->w);
         if (rc != IMM_OK) job_fail(*j, rc);
     }
+    t_p[1] = ms_since(tw0) - t_p[0];
     for (Job* j : S) {
         if (j->stage == 5) continue;
         bool progress = false;
+        const auto ta = std::chrono::steady_clock::now();
         int rc = cudaStreamSynchronize(j->w->stream) == cudaSuccess ? IMM_OK : IMM_ECUDA;
+        t_sync += ms_since(ta);
         if (rc == IMM_OK) rc = batch_phase3(j->w, &progress);
         if (rc != IMM_OK) job_fail(*j, rc);
         else if (j->w->nsets >= j->target) ++j->stage;
     }
     const double t_sample = ms_since(tw0);
+    t_p[2] = t_sample - t_p[0] - t_p[1];
+    if (trace_on() && !S.empty())
+        fprintf(stderr, "imm wave phases: %.2f / %.2f / %.2f ms, of which waiting on streams %.2f ms\n", t_p[0], t_p[1],
+                t_p[2], t_sync);
     // the previous wave's selection has run beside these phases
     const auto tc0 = std::chrono::steady_clock::now();
     const size_t collected = ws.inflight.size();
@@ -1850,6 +1901,7 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
     std::vector<Job*> active;
     uint64_t off = 0;
     int rc = IMM_OK;
+    const auto tb0 = std::chrono::steady_clock::now();
     for (uint32_t q = 0; q < nq; ++q) {
         Job& j = jobs[q];
         j.k = queries[q].k;
@@ -1858,6 +1910,10 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
         j.seed = queries[q].rng_seed;
         j.seeds_out = seeds_out + off;
         off += j.k;
+        // workers allocate through the graph context's allocator when it has
+        // one (a caching allocator hands each call's buffers back to the next
+        // call at once, which stream-ordered pool allocations from new
+        // streams measured about 2x slower)
         rc = make_worker(queries[q].graph, &j.w);
         if (rc != IMM_OK) break;
         rc = job_start(j);
@@ -1866,6 +1922,8 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
         rc = IMM_OK;
     }
     uint64_t launches = 0;
+    const double t_setup = ms_since(tb0);
+    const auto tb1 = std::chrono::steady_clock::now();
     {
         WaveState ws;
         while (rc == IMM_OK) {
@@ -1877,11 +1935,16 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
         // nothing may still run on the workers' buffers when they are freed
         cudaStreamSynchronize(g0->stream);
     }
+    const double t_waves = ms_since(tb1);
+    const auto tb2 = std::chrono::steady_clock::now();
     for (uint32_t q = 0; q < nq; ++q) {
         if (status_out) status_out[q] = jobs[q].stage == 4 ? IMM_OK : (jobs[q].status ? jobs[q].status : rc);
         if (stats_out) stats_out[q] = jobs[q].st;
         destroy_worker(jobs[q].w);
     }
+    if (trace_on())
+        fprintf(stderr, "imm batch: %u queries: set-up %.2f ms, waves %.2f ms, tear-down %.2f ms\n", nq, t_setup,
+                t_waves, ms_since(tb2));
     return rc;
 }
 
