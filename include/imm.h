@@ -220,6 +220,34 @@ typedef struct imm_opim_stats {
 int imm_run_opim(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell, uint64_t rng_seed,
                  uint32_t* seeds_out, imm_opim_stats* stats_out);
 
+/* ---- tuning (knobs that change speed, never results) ----
+ * Every RRR set is a pure function of (graph, seed, set id) and the greedy's
+ * picks do not depend on how the work is scheduled, so these knobs change
+ * how fast a run goes, not what it returns.
+ *   batch_sets        most sets sampled per batch (the arena grows by
+ *                     batches; smaller batches reuse less memory per step)
+ *   group_min_mean    mean size of the large IC sets (from earlier batches)
+ *                     from which solo runs sample them 64 at a time as one
+ *                     multi-source BFS (also needs >= n/64)
+ *   select_cta_max_n  solo selections on graphs up to this many vertices run
+ *                     on one CTA, larger ones on the cooperative grid
+ *   cluster_min_n     batched and served selections on graphs of at least
+ *                     this many vertices run on an 8-CTA thread-block
+ *                     cluster, smaller ones on one CTA
+ *   select_cand       nonzero: one-CTA and cluster selections scan a
+ *                     candidate list in rounds where it is exact
+ * Batch and server workers take the tuning of their graph's context. */
+typedef struct imm_tuning {
+    uint32_t batch_sets;
+    uint32_t group_min_mean;
+    uint32_t select_cta_max_n;
+    uint32_t cluster_min_n;
+    uint32_t select_cand;
+} imm_tuning;
+/* Errors: EINVAL (ctx or tuning NULL, batch_sets < 256). */
+int imm_set_tuning(imm_ctx* ctx, const imm_tuning* tuning);
+int imm_get_tuning(imm_ctx* ctx, imm_tuning* tuning_out);
+
 /* One query of a batch: the context holding its graph (loaded with
  * imm_load_graph; the model is the graph's), and IMM's parameters. */
 typedef struct imm_query {
@@ -249,6 +277,19 @@ typedef struct imm_query {
  * status_out while the others complete. */
 int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* seeds_out, imm_stats* stats_out,
                   int* status_out);
+
+/* Autotuner for batched IMM: runs the batch (imm_run_batch) once per
+ * candidate tuning of a fixed grid, each applied to every graph context of
+ * the batch, `reps` times each (the first run of each candidate is not
+ * timed when reps > 1), and keeps the fastest by host wall time: it is set
+ * on every graph context of the batch and written to *best_out (nullable).
+ * times_ms_out (host, nullable, IMM_TUNE_CANDIDATES entries) receives each
+ * candidate's mean time, and candidates_out (host, nullable, same count) the
+ * candidates.  The batch's results are the same under every candidate.
+ * Errors: as imm_run_batch (a query that fails fails the call). */
+#define IMM_TUNE_CANDIDATES 12
+int imm_autotune_batch(const imm_query* queries, uint32_t nq, uint32_t reps, imm_tuning* best_out,
+                       double* times_ms_out, imm_tuning* candidates_out);
 
 /* ---- served IMM (continuous batching) ----
  * A server keeps the given graphs resident (caller-owned contexts that must

@@ -41,7 +41,25 @@ struct Segment {
 };
 
 constexpr double kE = 2.71828182845904523536;  // the double nearest e
-constexpr uint32_t kSelectCtaMaxN = 1u << 17;  // graphs this small select in one CTA
+constexpr uint32_t kSelectCtaMaxN = 1u << 17;  // default: graphs this small select in one CTA
+
+imm_tuning default_tuning()
+{
+    imm_tuning t;
+    t.batch_sets = 1u << 22;
+    t.group_min_mean = 4096;
+    t.select_cta_max_n = kSelectCtaMaxN;
+    t.cluster_min_n = 1u << 15;
+    t.select_cand = 1;
+    return t;
+}
+
+// tests: environment overrides of two knobs (read once per process)
+uint32_t env_u32(const char* name, uint32_t dflt)
+{
+    const char* e = std::getenv(name);
+    return e ? (uint32_t)std::strtoul(e, nullptr, 10) : dflt;
+}
 constexpr size_t kServerIdlePerGraph = 8;       // workers a server keeps for reuse per graph
 
 }  // namespace
@@ -103,9 +121,10 @@ struct imm_ctx {
     DBuf cand, cstate;
 
     DBuf flags;
+    imm_tuning tune = default_tuning();
     uint64_t arena_limit = 0;
     uint64_t dev_bytes = 0;  // device bytes this context holds
-    uint32_t next_batch = 1u << 22;
+    uint32_t next_batch = 1u << 22;  // reset to tune.batch_sets with the stream
     double avg_len = 0.0;
     double small_mean = 0.0;  // running mean members per small-path set
     double large_mean = 0.0;  // running mean members per large-path set
@@ -308,7 +327,7 @@ void drop_stream(imm_ctx* c)
     c->avg_len = 0.0;
     c->small_mean = 0.0;
     c->large_mean = 0.0;
-    c->next_batch = 1u << 22;
+    c->next_batch = c->tune.batch_sets;
     if (c->off.p) cudaMemsetAsync(c->off.p, 0, sizeof(uint64_t), c->stream);
     if (c->cnt.p) cudaMemsetAsync(c->cnt.p, 0, (size_t)c->n * 4, c->stream);
     if (c->cnt_list.p) cudaMemsetAsync(c->cnt_list.p, 0, (size_t)c->n * 4, c->stream);
@@ -533,7 +552,7 @@ bool use_group(const imm_ctx* c, uint32_t large_count)
     if (!ic_group_supported(c->di)) return false;
     if (force && strcmp(force, "group") == 0) return true;
     if (large_count < kGroupSets) return false;
-    if (c->large_mean > 0.0) return c->large_mean >= std::max(4096.0, (double)c->n / 64.0);
+    if (c->large_mean > 0.0) return c->large_mean >= std::max((double)c->tune.group_min_mean, (double)c->n / 64.0);
     return c->n >= (1u << 19);
 }
 
@@ -815,7 +834,7 @@ int batch_phase3(imm_ctx* c, bool* progress)
     c->nbmp += nb;
     c->acc_edges += hs.edges;
     c->acc_sample_members += hs.all_members;
-    c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : (1u << 22);
+    c->next_batch = committed < count ? std::max<uint32_t>(256, (uint32_t)committed) : c->tune.batch_sets;
     // running mean of the small-path set sizes of this batch
     if (count > c->fb_large) {
         const double m = (double)hs.stage_cursor / (double)(count - c->fb_large);
@@ -926,9 +945,9 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     s.seeds = P<uint32_t>(c->seeds);
     s.segs = P<DevSegment>(c->dsegs);
     s.nsegs = (uint32_t)hsegs.size();
-    // IMM_SELECT_CAND=0 (tests): every argmax scans all n vertices
-    const char* cf = std::getenv("IMM_SELECT_CAND");
-    const bool cand = !(cf && std::strcmp(cf, "0") == 0);
+    // IMM_SELECT_CAND=0 (tests) overrides the tuning: every argmax scans all n vertices
+    static const uint32_t cand_env = env_u32("IMM_SELECT_CAND", 1u);
+    const bool cand = c->tune.select_cand && cand_env;
     s.cand = cand ? P<uint32_t>(c->cand) : nullptr;
     s.cstate = P<uint32_t>(c->cstate);
     // IMM_SELECT_MODE=decrement|rebuild (tests): one counter update for every
@@ -992,7 +1011,7 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     // all k rounds in one launch: one CTA for small graphs (block barriers),
     // the whole cooperative grid otherwise; per-round launches if the device
     // refuses a cooperative grid of that size
-    if (c->n <= kSelectCtaMaxN) {
+    if (c->n <= c->tune.select_cta_max_n) {
         TRY(ensure(c, c->dstate, sizeof(SelectState) + 16));
         c->pin->k = k;
         c->pin->state = s;
@@ -1100,6 +1119,8 @@ int make_worker(imm_ctx* g, imm_ctx** out, bool own_allocator = false)
     w->guide = g->guide;
     w->borrowed = true;
     w->arena_limit = g->arena_limit;
+    w->tune = g->tune;
+    w->next_batch = w->tune.batch_sets;
     *out = w;
     int rc = dalloc(w, w->cnt, (size_t)w->n * 4);
     if (rc == IMM_OK) rc = dalloc(w, w->cnt_list, (size_t)w->n * 4);
@@ -1246,16 +1267,14 @@ double ms_since(std::chrono::steady_clock::time_point t)
 // other queries; that wave collects it (waiting only if it is still running)
 // before it launches its own.  The jobs of an in-flight selection neither
 // sample nor select until collected.
-// Instances on graphs of at least this many vertices select with a cluster
-// of CTAs (IMM_SELECT_CLUSTER_MIN_N overrides it; tests use 0 to send every
-// instance there, and a value above every n keeps one CTA per instance).
-uint32_t select_cluster_min_n()
+// Instances on graphs of at least tune.cluster_min_n vertices select with a
+// cluster of CTAs (IMM_SELECT_CLUSTER_MIN_N overrides every tuning; tests use
+// 0 to send every instance there, and a value above every n keeps one CTA
+// per instance).
+uint32_t select_cluster_min_n(const imm_ctx* w)
 {
-    static const uint32_t v = [] {
-        const char* e = std::getenv("IMM_SELECT_CLUSTER_MIN_N");
-        return e ? (uint32_t)std::strtoul(e, nullptr, 10) : (1u << 15);
-    }();
-    return v;
+    static const char* e = std::getenv("IMM_SELECT_CLUSTER_MIN_N");
+    return e ? (uint32_t)std::strtoul(e, nullptr, 10) : w->tune.cluster_min_n;
 }
 
 struct WaveState {
@@ -1356,9 +1375,10 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
         prc[t] = select_prepare(L[t]->w, L[t]->k, &prep[t], L[t]->target);
         if (prc[t] == IMM_OK) cudaEventRecord(L[t]->w->ev[4], L[t]->w->stream);
     }
-    // instances on graphs of >= cluster_min_n vertices select with a cluster
-    // of CTAs each, the others with one CTA; the small ones come first
-    const uint32_t cluster_min_n = select_cluster_min_n();
+    // instances on graphs of >= their tuning's cluster_min_n vertices select
+    // with a cluster of CTAs each, the others with one CTA; the small ones
+    // come first
+    auto big = [](const Job* j) { return j->w->n >= select_cluster_min_n(j->w); };
     for (int pass = 0; pass < 2; ++pass) {
         for (size_t t = 0; t < L.size(); ++t) {
             Job* j = L[t];
@@ -1366,7 +1386,7 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
                 if (pass == 0) job_fail(*j, prc[t]);
                 continue;
             }
-            if ((j->w->n >= cluster_min_n) != (pass == 1)) continue;
+            if (big(j) != (pass == 1)) continue;
             states[ok.size()] = prep[t];
             ks[ok.size()] = j->k;
             cudaStreamWaitEvent(master, j->w->ev[4], 0);
@@ -1375,7 +1395,7 @@ int run_wave(std::vector<Job*>& jobs, imm_ctx* host, cudaStream_t master, uint64
     }
     if (ok.empty()) return IMM_OK;
     uint32_t nsmall = 0;
-    while (nsmall < ok.size() && ok[nsmall]->w->n < cluster_min_n) ++nsmall;
+    while (nsmall < ok.size() && !big(ok[nsmall])) ++nsmall;
     const size_t nbytes = ok.size() * (rec + 4) + 16;
     TRY(ensure(host, host->bstates, nbytes));
     // the states are staged through pinned memory the host context keeps
@@ -1946,6 +1966,96 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
         fprintf(stderr, "imm batch: %u queries: set-up %.2f ms, waves %.2f ms, tear-down %.2f ms\n", nq, t_setup,
                 t_waves, ms_since(tb2));
     return rc;
+}
+
+extern "C" int imm_set_tuning(imm_ctx* c, const imm_tuning* t)
+{
+    if (!c || !t) return IMM_EINVAL;
+    if (t->batch_sets < 256) return set_err(c, IMM_EINVAL, "batch_sets must be >= 256");
+    c->tune = *t;
+    if (c->nsets == 0) c->next_batch = c->tune.batch_sets;
+    return IMM_OK;
+}
+
+extern "C" int imm_get_tuning(imm_ctx* c, imm_tuning* out)
+{
+    if (!c || !out) return IMM_EINVAL;
+    *out = c->tune;
+    return IMM_OK;
+}
+
+// The autotuner's grid: the selection team threshold of batched instances
+// (cluster from 2^12, 2^14, 2^16 vertices, or never) crossed with the
+// candidate-list argmax on or off and two sampling batch sizes.
+static void tune_candidates(const imm_tuning& base, imm_tuning* out)
+{
+    const uint32_t cmin[4] = {1u << 12, 1u << 14, 1u << 16, 0xFFFFFFFFu};
+    const uint32_t cand[3] = {1u, 0u, 1u};
+    const uint32_t bsets[3] = {1u << 22, 1u << 22, 1u << 16};
+    int i = 0;
+    for (uint32_t a = 0; a < 4; ++a) {
+        for (uint32_t b = 0; b < 3; ++b) {
+            imm_tuning t = base;
+            t.cluster_min_n = cmin[a];
+            t.select_cand = cand[b];
+            t.batch_sets = bsets[b];
+            out[i++] = t;
+        }
+    }
+}
+
+extern "C" int imm_autotune_batch(const imm_query* queries, uint32_t nq, uint32_t reps, imm_tuning* best_out,
+                                  double* times_ms_out, imm_tuning* candidates_out)
+{
+    if (nq == 0 || !queries) return IMM_EINVAL;
+    std::vector<imm_ctx*> graphs;
+    uint64_t total_k = 0;
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (!queries[q].graph) return IMM_EINVAL;
+        if (std::find(graphs.begin(), graphs.end(), queries[q].graph) == graphs.end())
+            graphs.push_back(queries[q].graph);
+        total_k += queries[q].k;
+    }
+    if (reps == 0) reps = 1;
+    std::vector<imm_tuning> saved;
+    for (imm_ctx* g : graphs) saved.push_back(g->tune);
+    imm_tuning cands[IMM_TUNE_CANDIDATES];
+    tune_candidates(graphs[0]->tune, cands);
+    std::vector<uint32_t> seeds(std::max<uint64_t>(total_k, 1));
+    std::vector<int> status(nq);
+    double best_ms = 0.0;
+    int best = -1, rc = IMM_OK;
+    for (int i = 0; i < IMM_TUNE_CANDIDATES && rc == IMM_OK; ++i) {
+        for (imm_ctx* g : graphs) g->tune = cands[i];
+        double sum = 0.0;
+        uint32_t timed = 0;
+        const uint32_t runs = reps > 1 ? reps + 1 : 1;
+        for (uint32_t r = 0; r < runs && rc == IMM_OK; ++r) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = imm_run_batch(queries, nq, seeds.data(), nullptr, status.data());
+            const double ms = ms_since(t0);
+            for (uint32_t q = 0; q < nq && rc == IMM_OK; ++q)
+                if (status[q] != IMM_OK) rc = status[q];
+            if (reps == 1 || r > 0) {
+                sum += ms;
+                ++timed;
+            }
+        }
+        const double mean = timed ? sum / timed : 0.0;
+        if (times_ms_out) times_ms_out[i] = mean;
+        if (rc == IMM_OK && (best < 0 || mean < best_ms)) {
+            best = i;
+            best_ms = mean;
+        }
+    }
+    if (rc != IMM_OK || best < 0) {
+        for (size_t i = 0; i < graphs.size(); ++i) graphs[i]->tune = saved[i];
+        return rc != IMM_OK ? rc : IMM_EINVAL;
+    }
+    for (imm_ctx* g : graphs) g->tune = cands[best];
+    if (best_out) *best_out = cands[best];
+    if (candidates_out) std::memcpy(candidates_out, cands, sizeof(cands));
+    return IMM_OK;
 }
 
 // ===========================================================================

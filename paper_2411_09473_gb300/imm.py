@@ -86,6 +86,18 @@ class imm_opim_stats(ctypes.Structure):
 IMM_OPIM_KEY = 0xD1B54A32D192ED03
 
 
+class imm_tuning(ctypes.Structure):
+    _fields_ = [("batch_sets", ctypes.c_uint32), ("group_min_mean", ctypes.c_uint32),
+                ("select_cta_max_n", ctypes.c_uint32), ("cluster_min_n", ctypes.c_uint32),
+                ("select_cand", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+IMM_TUNE_CANDIDATES = 12
+
+
 class imm_server_config(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32),
                 ("share_streams", ctypes.c_uint32)]
@@ -137,6 +149,9 @@ def _load():
         "imm_run": ([vp, i32, u32, f64, f64, u64, vp, ctypes.POINTER(imm_stats)], i32),
         "imm_run_ex": ([vp, i32, u32, f64, f64, u64, u32, vp, ctypes.POINTER(imm_stats)], i32),
         "imm_run_opim": ([vp, i32, u32, f64, f64, u64, vp, ctypes.POINTER(imm_opim_stats)], i32),
+        "imm_set_tuning": ([vp, ctypes.POINTER(imm_tuning)], i32),
+        "imm_get_tuning": ([vp, ctypes.POINTER(imm_tuning)], i32),
+        "imm_autotune_batch": ([vp, u32, u32, ctypes.POINTER(imm_tuning), vp, vp], i32),
         "imm_reset_sets": ([vp], i32),
         "imm_stream_size": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
         "imm_get_set": ([vp, u64, vp, u32, ctypes.POINTER(u32)], i32),
@@ -287,6 +302,36 @@ def imm_run_opim(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_
     _check(ctx, _load().imm_run_opim(ctx.handle, model, k, epsilon, ell, rng_seed, seeds.ctypes.data,
                                      ctypes.byref(st)))
     return seeds[:k], st
+
+
+def imm_set_tuning(ctx: _Ctx, **knobs) -> None:
+    """Change knobs of the context's tuning (see imm_tuning); speed only."""
+    t = imm_tuning()
+    _check(ctx, _load().imm_get_tuning(ctx.handle, ctypes.byref(t)))
+    for k, v in knobs.items():
+        setattr(t, k, v)
+    _check(ctx, _load().imm_set_tuning(ctx.handle, ctypes.byref(t)))
+
+
+def imm_get_tuning(ctx: _Ctx) -> dict:
+    t = imm_tuning()
+    _check(ctx, _load().imm_get_tuning(ctx.handle, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def imm_autotune_batch(queries, reps: int = 1):
+    """Autotune a batch: (best tuning dict, [(candidate dict, mean ms)])."""
+    nq = len(queries)
+    arr = (imm_query * max(nq, 1))()
+    for i, (g, k, eps, ell, seed) in enumerate(queries):
+        arr[i] = imm_query(g.handle, k, eps, ell, seed)
+    best = imm_tuning()
+    times = np.zeros(IMM_TUNE_CANDIDATES, dtype=np.float64)
+    cands = (imm_tuning * IMM_TUNE_CANDIDATES)()
+    rc = _load().imm_autotune_batch(arr, nq, reps, ctypes.byref(best), times.ctypes.data, cands)
+    if rc != IMM_OK:
+        raise ImmError(rc, "imm_autotune_batch failed")
+    return best.as_dict(), [(cands[i].as_dict(), float(times[i])) for i in range(IMM_TUNE_CANDIDATES)]
 
 
 def imm_run_batch(queries):
