@@ -372,6 +372,16 @@ int imm_get_counts(imm_ctx* ctx, uint32_t* cnt_out);
  * (0 = unlimited).  imm_sample returns ENOMEM instead of growing past it. */
 int imm_set_arena_limit(imm_ctx* ctx, uint64_t bytes);
 
+/* Properties of the loaded build: IMM_BUILD_BOUNDS_CHECK is set when the
+ * library was compiled with index checks (-DIMM_BOUNDS_CHECK).  That build
+ * compares indices into the stream arena, the sampling staging and output
+ * buffers, the per-set queues, the grouped sampler's lists and the
+ * selection's lists with their bounds; the first index out of range is not
+ * used, the kernels record it, and the call returns IMM_ECUDA naming the
+ * check, the index and the bound. */
+#define IMM_BUILD_BOUNDS_CHECK 1
+int imm_build_flags(void);
+
 /* ---- selection without device allocation ----
  * No counterpart in the paper: this entry point exists for callers that
  * cannot allocate device memory at run time, for example a plugin inside

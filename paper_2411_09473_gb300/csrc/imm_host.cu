@@ -16,6 +16,7 @@
 #include <unordered_map>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -501,6 +502,12 @@ cudaError_t coop_launch(int device, cudaStream_t st, F&& launch)
     return cudaEventRecord(o.last, st);
 }
 
+// The error word of the bounds-checked build inside the batch scalars.
+unsigned long long* batch_bounds(imm_ctx* c)
+{
+    return reinterpret_cast<unsigned long long*>(static_cast<char*>(c->scalars.p) + offsetof(BatchScalars, bounds));
+}
+
 // Scratch of the grouped IC large path (carved from one buffer; the masks
 // start at zero and every launch leaves them zero).
 int ensure_group(imm_ctx* c, GroupScratch* gs)
@@ -533,6 +540,10 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     gs->he = reinterpret_cast<uint4*>(p + o_he);
     gs->stride = slot;
     gs->ctr = reinterpret_cast<GroupCounters*>(p + o_ct);
+    gs->wcap = (uint32_t)wcap;
+    gs->hcap = (uint32_t)hcap;
+    gs->lcap = c->n;
+    gs->bounds = batch_bounds(c);
     return IMM_OK;
 }
 
@@ -554,6 +565,20 @@ bool use_group(const imm_ctx* c, uint32_t large_count)
     if (large_count < kGroupSets) return false;
     if (c->large_mean > 0.0) return c->large_mean >= std::max((double)c->tune.group_min_mean, (double)c->n / 64.0);
     return c->n >= (1u << 19);
+}
+
+// Checked builds: the first failed index check recorded by the kernels
+// enqueued so far on the context's stream (`err` is a device error word);
+// IMM_ECUDA naming it, else IMM_OK.  A no-op in normal builds.
+int bounds_verdict(imm_ctx* c, const unsigned long long* err, const char* where)
+{
+    if (!kBoundsChecked) return IMM_OK;
+    unsigned long long h[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h[0])
+        return set_err(c, IMM_ECUDA, "%s: index check %llu failed (index %llu, bound %llu)", where, h[0], h[1], h[2]);
+    return IMM_OK;
 }
 
 int index_limit_ok(imm_ctx* c, uint64_t more_bytes)
@@ -582,7 +607,8 @@ int merge_segments(imm_ctx* c)
     CK(launch_vertex_scan(P<uint32_t>(c->cnt_list), c->n, P<uint64_t>(seg.voff), nullptr, nullptr,
                           P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di, c->stream));
     CK(launch_index_scatter(0, c->nsets, P<uint64_t>(c->off), P<uint32_t>(c->arena), P<uint64_t>(seg.voff),
-                            P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di, c->stream));
+                            P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), std::max<uint64_t>(c->list_members, 1),
+                            batch_bounds(c), c->di, c->stream));
     c->acc_launches += 4;
     c->index_bytes = seg.voff.bytes + seg.inv.bytes;
     c->segs.push_back(seg);
@@ -755,6 +781,8 @@ int batch_phase2(imm_ctx* c)
     o.bmp_len = P<uint32_t>(c->bmp_len);
     o.bmp_rel = P<uint32_t>(c->bmp_rel);
     o.bmp_base = c->nbmp;
+    o.arena_cap = c->arena_cap;
+    o.bounds = batch_bounds(c);
     CK(launch_batch_scan(b, o, P<uint64_t>(c->scan_tmp), c->di, c->stream));
     c->acc_launches += 3;
     CK(cudaMemcpyAsync(&c->pin->sc, b.sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, c->stream));
@@ -772,6 +800,9 @@ int batch_phase3(imm_ctx* c, bool* progress)
     const uint32_t count = b.count;
     *progress = false;
     if (hs.error) return set_err(c, IMM_ECUDA, "sampler reported device error 0x%x", hs.error);
+    if (hs.bounds[0])
+        return set_err(c, IMM_ECUDA, "sampling: index check %llu failed (index %llu, bound %llu)", hs.bounds[0],
+                       hs.bounds[1], hs.bounds[2]);
     const uint64_t committed = hs.committed;
     const uint64_t lm = hs.list_members;
     const uint64_t nb = hs.nbitmaps;
@@ -806,6 +837,7 @@ int batch_phase3(imm_ctx* c, bool* progress)
     o.bmp = P<uint32_t>(c->bmp);
     o.bmp_set = P<uint32_t>(c->bmp_set);
     o.bmp_len = P<uint32_t>(c->bmp_len);
+    o.arena_cap = c->arena_cap;
     Segment seg;
     seg.set_begin = c->nsets;
     seg.set_end = c->nsets + committed;
@@ -822,7 +854,8 @@ int batch_phase3(imm_ctx* c, bool* progress)
                           P<uint32_t>(c->cnt_list), P<uint32_t>(c->cursor), P<uint64_t>(c->vtmp), c->di,
                           c->stream));
     CK(launch_index_scatter(seg.set_begin, seg.set_end, P<uint64_t>(c->off), P<uint32_t>(c->arena),
-                            P<uint64_t>(seg.voff), P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), c->di, c->stream));
+                            P<uint64_t>(seg.voff), P<uint32_t>(c->cursor), P<uint32_t>(seg.inv), std::max<uint64_t>(lm, 1),
+                            batch_bounds(c), c->di, c->stream));
     CK(cudaEventRecord(c->ev[7], c->stream));
     c->index_timed = true;
     c->acc_launches += nb ? 7 : 5;
@@ -845,6 +878,7 @@ int batch_phase3(imm_ctx* c, bool* progress)
         c->large_mean = c->large_mean > 0 ? 0.5 * (c->large_mean + m) : m;
     }
     if (c->segs.size() > 48) TRY(merge_segments(c));
+    TRY(bounds_verdict(c, batch_bounds(c), "compaction and index"));
     *progress = true;
     return IMM_OK;
 }
@@ -892,7 +926,7 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     TRY(ensure(c, c->ubmp_n, (size_t)k * 8));
     TRY(ensure(c, c->seeds, (size_t)k * 4));
     TRY(ensure(c, c->cand, (size_t)c->n * 4));
-    TRY(ensure(c, c->cstate, 16));
+    TRY(ensure(c, c->cstate, 64));
     std::vector<DevSegment> hsegs;
     for (auto& sg : c->segs) hsegs.push_back(DevSegment{P<uint64_t>(sg.voff), P<uint32_t>(sg.inv)});
     TRY(ensure(c, c->dsegs, std::max<size_t>(hsegs.size(), 1) * sizeof(DevSegment)));
@@ -916,7 +950,7 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     if (part) CK(cudaMemsetAsync(P<uint8_t>(c->covered) + prefix, 1, R - prefix, c->stream));
     DBuf* zero_k[] = {&c->keys, &c->newly_n, &c->vol_cov, &c->vol_list, &c->bmp_cov, &c->ubmp_n};
     for (DBuf* z : zero_k) CK(cudaMemsetAsync(z->p, 0, (size_t)k * 8, c->stream));
-    CK(cudaMemsetAsync(c->cstate.p, 0, 16, c->stream));
+    CK(cudaMemsetAsync(c->cstate.p, 0, 64, c->stream));
 
     SelectState& s = *out;
     s.n = c->n;
@@ -950,6 +984,7 @@ int select_prepare(imm_ctx* c, uint32_t k, SelectState* out, uint64_t prefix = ~
     const bool cand = c->tune.select_cand && cand_env;
     s.cand = cand ? P<uint32_t>(c->cand) : nullptr;
     s.cstate = P<uint32_t>(c->cstate);
+    s.bounds = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->cstate.p) + 32);
     // IMM_SELECT_MODE=decrement|rebuild (tests): one counter update for every
     // round; the two give the same counts (Sec. IV-C), which the tests check
     s.force_mode = 0;
@@ -1038,6 +1073,7 @@ int select_k(imm_ctx* c, uint32_t k, uint32_t* seeds_out, uint64_t* covered_out)
     CK(cudaEventRecord(c->ev[5], c->stream));
     TRY(select_readback(c, k, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    TRY(bounds_verdict(c, reinterpret_cast<unsigned long long*>(static_cast<char*>(c->cstate.p) + 32), "selection"));
     c->acc_select_ms += elapsed(c, 4, 5);
     const uint64_t cov = select_covered(c, k, seeds_out);
     if (covered_out) *covered_out = cov;
@@ -1298,7 +1334,9 @@ int collect_selection(WaveState& ws, imm_ctx* host)
     }
     for (Job* j : L) {
         const uint64_t cov = select_covered(j->w, j->k, nullptr);
-        int rc = job_after_select(*j, cov);
+        int rc = bounds_verdict(j->w, reinterpret_cast<unsigned long long*>(static_cast<char*>(j->w->cstate.p) + 32),
+                                "selection");
+        if (rc == IMM_OK) rc = job_after_select(*j, cov);
         if (rc == IMM_OK && (j->stage == 0 || j->stage == 2)) rc = begin_stream(j->w, j->target, j->seed);
         if (rc != IMM_OK) job_fail(*j, rc);
     }
@@ -1966,6 +2004,11 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
         fprintf(stderr, "imm batch: %u queries: set-up %.2f ms, waves %.2f ms, tear-down %.2f ms\n", nq, t_setup,
                 t_waves, ms_since(tb2));
     return rc;
+}
+
+extern "C" int imm_build_flags(void)
+{
+    return kBoundsChecked ? IMM_BUILD_BOUNDS_CHECK : 0;
 }
 
 extern "C" int imm_set_tuning(imm_ctx* c, const imm_tuning* t)

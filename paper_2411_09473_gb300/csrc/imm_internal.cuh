@@ -154,6 +154,35 @@ struct BatchScalars {
     unsigned long long nbitmaps;      // kept sets stored as bitmaps
     int error;
     int pad;
+    unsigned long long bounds[3];     // checked builds: first failed index check (where, index, bound)
+};
+
+// Index checks of the bounds-checked build (-DIMM_BOUNDS_CHECK): an index at
+// or above its buffer's bound is not used; the first such index is recorded
+// as (where, index, bound) in a device error word that the host reads after
+// the launch and reports.  In the normal build the check is `true` and
+// compiles away.
+#ifdef IMM_BOUNDS_CHECK
+__device__ __forceinline__ bool imm_in_bounds(uint64_t idx, uint64_t bound, unsigned long long* err, uint32_t where)
+{
+    if (idx < bound) return true;
+    if (atomicCAS(err, 0ull, (unsigned long long)where) == 0ull) {
+        err[1] = idx;
+        err[2] = bound;
+    }
+    return false;
+}
+#define IMM_IN_BOUNDS(idx, bound, err, where) \
+    ::imm::imm_in_bounds((uint64_t)(idx), (uint64_t)(bound), (err), (uint32_t)(where))
+constexpr bool kBoundsChecked = true;
+#else
+#define IMM_IN_BOUNDS(idx, bound, err, where) true
+constexpr bool kBoundsChecked = false;
+#endif
+// where codes of the checks
+enum : uint32_t {
+    kChkStage = 1, kChkLargeQ, kChkSlotQueue, kChkSlotBitmap, kChkBig, kChkArena, kChkInv, kChkGroupSmall,
+    kChkGroupWin, kChkGroupLarge, kChkNewly, kChkCand, kChkUbmp, kChkCounts
 };
 
 constexpr uint64_t kBigFlag = 1ull << 63;  // set_pos points into the large-output buffer
@@ -223,6 +252,8 @@ struct BatchOut {
     uint32_t* bmp_len;    // [nbmp] members of each bitmap set
     uint32_t* bmp_rel;    // [count] batch-relative id of the batch's r-th bitmap
     uint64_t bmp_base;    // bitmaps stored before this batch
+    uint64_t arena_cap;   // entries of arena
+    unsigned long long* bounds;  // checked builds: the batch's error word (BatchScalars::bounds)
 };
 
 // ---------------------------------------------------------------------------
@@ -276,6 +307,9 @@ struct GroupScratch {
     uint4* he;                // [hcap] large vertices: (rs, re, F lo, F hi)
     uint64_t stride;          // bytes from each slot's arrays to the next slot's
     GroupCounters* ctr;       // [kGroupSlots], one per slot (ctr[0].claim serves all)
+    uint32_t wcap, hcap;      // entries of wst and of hb / he
+    uint32_t lcap;            // entries of lq / lpre (n)
+    unsigned long long* bounds;  // checked builds: the batch's error word
 };
 int ic_group_supported(const DeviceInfo& di);
 uint64_t ic_group_heavy_cap(uint32_t n, uint64_t m);
@@ -298,9 +332,9 @@ cudaError_t launch_bitmap_count(const uint32_t* bmp, uint32_t words, uint32_t n,
 // (each nullable); cursor zeroed
 cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff, uint32_t* cnt, uint32_t* cnt2,
                                uint32_t* cursor, uint64_t* tmp, const DeviceInfo& di, cudaStream_t st);
-cudaError_t launch_index_scatter(uint64_t set_begin, uint64_t set_end, const uint64_t* off,
-                                 const uint32_t* arena, const uint64_t* voff, uint32_t* cursor,
-                                 uint32_t* inv, const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_index_scatter(uint64_t set_begin, uint64_t set_end, const uint64_t* off, const uint32_t* arena,
+                                 const uint64_t* voff, uint32_t* cursor, uint32_t* inv, uint64_t inv_cap,
+                                 unsigned long long* err, const DeviceInfo& di, cudaStream_t st);
 
 // selection
 struct SelectState {
@@ -333,6 +367,7 @@ struct SelectState {
     int force_mode;      // 0: decrement or recount chosen per round; 1: always decrement; 2: always recount
     uint32_t* cand;      // n (nullable): argmax candidates, the unpicked vertices with counts >= tau
     uint32_t* cstate;    // 4: candidates, tau, list valid, count of the last list that came out too long
+    unsigned long long* bounds;  // 3: checked builds, first failed index check (where, index, bound)
 };
 cudaError_t launch_select_round(const SelectState& s, uint32_t j, const DeviceInfo& di, cudaStream_t st,
                                 uint64_t* launches);

@@ -259,6 +259,8 @@ struct SlotArrays {
     uint4 *lq, *he;
     uint32_t *lpre, *wst, *hb;
     GroupCounters* ct;
+    uint32_t lcap, wcap, hcap;  // entries of lq / lpre, wst, hb / he
+    unsigned long long* err;    // checked builds: the batch's error word
 };
 
 __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32_t k)
@@ -274,6 +276,10 @@ __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32
     a.wst = at(gs.wst);
     a.hb = at(gs.hb);
     a.ct = gs.ctr + k;
+    a.lcap = gs.lcap;
+    a.wcap = gs.wcap;
+    a.hcap = gs.hcap;
+    a.err = gs.bounds;
     return a;
 }
 
@@ -285,6 +291,7 @@ __device__ __forceinline__ void list_large(const SlotArrays& a, uint32_t par, ui
     const unsigned long long old =
         atomicAdd(&a.ct->hpack[par], (1ull << kPackShift) | (unsigned long long)((nq + kChunkQuads - 1) / kChunkQuads));
     const uint32_t i = (uint32_t)(old >> kPackShift);
+    if (!IMM_IN_BOUNDS(i, a.hcap, a.err, kChkGroupLarge)) return;
     a.hb[i] = (uint32_t)(old & kPackLow);
     a.he[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
 }
@@ -296,10 +303,11 @@ __device__ __forceinline__ void list_large(const SlotArrays& a, uint32_t par, ui
 __device__ __forceinline__ void list_small(const SlotArrays& a, uint32_t i, uint32_t off, uint32_t rs,
                                            uint32_t re, uint32_t nq, unsigned long long F)
 {
+    if (!IMM_IN_BOUNDS(i, a.lcap, a.err, kChkGroupSmall)) return;
     a.lq[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
     a.lpre[i] = off;
     const uint32_t w = (off + 31) >> 5;
-    if ((w << 5) < off + nq) a.wst[w] = i;
+    if ((w << 5) < off + nq && IMM_IN_BOUNDS(w, a.wcap, a.err, kChkGroupWin)) a.wst[w] = i;
 }
 
 // What a slot does in the current step (the same in every CTA: each CTA's
@@ -496,12 +504,15 @@ __device__ __forceinline__ void write_item(const DevGraph& g, const SampleBatch&
                     uint32_t base = 0;
                     if (lane == 0) base = (uint32_t)atomicAdd(&a.ct->lcur[s], (unsigned long long)__popc(bal));
                     base = __shfl_sync(kFull, base, 0);
-                    if (in) b.big[s_pos[s] + base + __popc(bal & lanemask_lt_g())] = u;
+                    const uint64_t at = s_pos[s] + base + __popc(bal & lanemask_lt_g());
+                    if (in && IMM_IN_BOUNDS(at, b.big_cap, a.err, kChkBig)) b.big[at] = u;
                 }
             }
         }
-        if (lane < G && s_kind[lane] == 1) b.big[s_pos[lane] + w] = mine0;
-        if (lane + 32 < G && s_kind[lane + 32] == 1) b.big[s_pos[lane + 32] + w] = mine1;
+        if (lane < G && s_kind[lane] == 1 && IMM_IN_BOUNDS(s_pos[lane] + w, b.big_cap, a.err, kChkBig))
+            b.big[s_pos[lane] + w] = mine0;
+        if (lane + 32 < G && s_kind[lane + 32] == 1 && IMM_IN_BOUNDS(s_pos[lane + 32] + w, b.big_cap, a.err, kChkBig))
+            b.big[s_pos[lane + 32] + w] = mine1;
     }
 }
 

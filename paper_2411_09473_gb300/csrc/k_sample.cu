@@ -224,7 +224,7 @@ ic_small_kernel(DevGraph g, SampleBatch b)
         if (overflow) {
             if (lane == 0) {
                 const uint32_t qi = atomicAdd(&b.sc->large_count, 1u);
-                b.large_q[qi] = rel;
+                if (IMM_IN_BOUNDS(qi, b.count, b.sc->bounds, kChkLargeQ)) b.large_q[qi] = rel;
                 b.set_len[rel] = kLenPending;
             }
             for (uint32_t i = lane; i < kSmallHash; i += 32) hash[i] = kEmpty;
@@ -240,7 +240,8 @@ ic_small_kernel(DevGraph g, SampleBatch b)
             ok = __shfl_sync(kFull, ok, 0);
             pos = shfl64(pos, 0);
             if (ok)
-                for (uint32_t i = lane; i < tail; i += 32) b.stage[pos + i] = list[i];
+                for (uint32_t i = lane; i < tail; i += 32)
+                    if (IMM_IN_BOUNDS(pos + i, b.stage_cap, b.sc->bounds, kChkStage)) b.stage[pos + i] = list[i];
             for (uint32_t i = lane; i < tail; i += 32) hash[lslot[i]] = kEmpty;
         }
         __syncwarp();
@@ -268,22 +269,26 @@ constexpr int kLargeThreads = 1024;
 // Test-and-set of u in the visited bitmap; appends u to the member queue when
 // it was not yet visited.  Bits only ever go from 0 to 1, so a plain read
 // that sees the bit set is final and saves the atomic.
-__device__ __forceinline__ void visit(uint32_t u, uint32_t* bm, uint32_t* q, uint32_t* s_tail)
+__device__ __forceinline__ void visit(uint32_t u, uint32_t* bm, uint32_t* q, uint32_t* s_tail,
+                                      unsigned long long* err, uint32_t qcap)
 {
     const uint32_t bit = 1u << (u & 31);
     uint32_t* word = bm + (u >> 5);
     if (*reinterpret_cast<volatile uint32_t*>(word) & bit) return;
     const uint32_t old = atomicOr(word, bit);
-    if (!(old & bit)) q[atomicAdd(s_tail, 1u)] = u;
+    if (!(old & bit)) {
+        const uint32_t at = atomicAdd(s_tail, 1u);
+        if (IMM_IN_BOUNDS(at, qcap, err, kChkSlotQueue)) q[at] = u;
+    }
 }
 
 __device__ __forceinline__ void visit_live(uint32_t live, uint32_t quad, const uint32_t* src, uint32_t* bm,
-                                           uint32_t* q, uint32_t* s_tail)
+                                           uint32_t* q, uint32_t* s_tail, unsigned long long* err, uint32_t qcap)
 {
     while (live) {
         const int t = __ffs(live) - 1;
         live &= live - 1;
-        visit(__ldg(src + (quad << 2) + t), bm, q, s_tail);
+        visit(__ldg(src + (quad << 2) + t), bm, q, s_tail, err, qcap);
     }
 }
 
@@ -291,7 +296,7 @@ constexpr uint32_t kWarpBuf = 128;
 __device__ __forceinline__ void expand_pair(uint32_t qa, bool ha, uint32_t rsa, uint32_t rea, uint32_t qb, bool hb,
                                             uint32_t rsb, uint32_t reb, const PhiloxSet& ps, const PhiloxKeys& rk,
                                             const DevGraph& g, uint32_t* bm, uint32_t* q, uint32_t* s_tail,
-                                            uint32_t* wbuf)
+                                            uint32_t* wbuf, unsigned long long* err, uint32_t qcap)
 {
     uint4 tha = make_uint4(0, 0, 0, 0), thb = tha, wa = tha, wb = tha;
     if (ha) tha = load_thr4(g.thr, qa);
@@ -311,15 +316,15 @@ __device__ __forceinline__ void expand_pair(uint32_t qa, bool ha, uint32_t rsa, 
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
     if (total > kWarpBuf) {
-        visit_live(la, qa, g.src, bm, q, s_tail);
-        visit_live(lb, qb, g.src, bm, q, s_tail);
+        visit_live(la, qa, g.src, bm, q, s_tail, err, qcap);
+        visit_live(lb, qb, g.src, bm, q, s_tail, err, qcap);
         return;
     }
     uint32_t p = incl - cnt;
     while (la) { const int t = __ffs(la) - 1; la &= la - 1; wbuf[p++] = (qa << 2) + t; }
     while (lb) { const int t = __ffs(lb) - 1; lb &= lb - 1; wbuf[p++] = (qb << 2) + t; }
     __syncwarp();
-    for (uint32_t i = lane; i < total; i += 32) visit(__ldg(g.src + wbuf[i]), bm, q, s_tail);
+    for (uint32_t i = lane; i < total; i += 32) visit(__ldg(g.src + wbuf[i]), bm, q, s_tail, err, qcap);
     __syncwarp();
 }
 
@@ -339,6 +344,8 @@ template <bool kSmemBitmap>
 __global__ void __launch_bounds__(kLargeThreads, 1)
 ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
 {
+    unsigned long long* const err = b.sc->bounds;
+    const uint32_t qcap = (uint32_t)ls.queue_cap;
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_wbuf[32][kWarpBuf];
@@ -421,7 +428,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     for (uint32_t q0 = (ors >> 2); q0 <= q1; q0 += 64) {
                         const uint32_t qa = q0 + lane;
                         expand_pair(qa, qa <= q1, ors, ore, qa + 32, qa + 32 <= q1, ors, ore, ps, b.rk, g, bm,
-                                    q, &s_tail, wbuf);
+                                    q, &s_tail, wbuf, err, qcap);
                     }
                 }
                 // light vertices: quads flattened across lanes, two per lane
@@ -450,7 +457,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     const bool ha = ja < total, hb = jb < total;
                     const uint32_t qa = (rsa >> 2) + (ja - exa);
                     const uint32_t qb = (rsb >> 2) + (jb - exb);
-                    expand_pair(qa, ha, rsa, rea, qb, hb, rsb, reb, ps, b.rk, g, bm, q, &s_tail, wbuf);
+                    expand_pair(qa, ha, rsa, rea, qb, hb, rsb, reb, ps, b.rk, g, bm, q, &s_tail, wbuf, err, qcap);
                 }
             }
             __syncthreads();
@@ -516,7 +523,7 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
                     const uint32_t q1 = (hre - 1) >> 2;
                     const uint32_t qa = (hrs >> 2) + (c - s_hpre[lo]) * kChunkQuads + lane;
                     expand_pair(qa, qa <= q1, hrs, hre, qa + 32, qa + 32 <= q1, hrs, hre, ps, b.rk, g, bm, q,
-                                &s_tail, wbuf);
+                                &s_tail, wbuf, err, qcap);
                 }
             }
             __syncthreads();
@@ -549,9 +556,11 @@ ic_large_kernel(DevGraph g, SampleBatch b, LargeSlots ls, uint32_t hcap)
         if (s_ok) {
             uint32_t* out = b.big + s_pos;
             if (kind) {
-                for (uint32_t i = tid; i < words; i += kLargeThreads) out[i] = bm[i];
+                for (uint32_t i = tid; i < words; i += kLargeThreads)
+                    if (IMM_IN_BOUNDS(s_pos + i, b.big_cap, err, kChkBig)) out[i] = bm[i];
             } else {
-                for (uint32_t i = tid; i < len; i += kLargeThreads) out[i] = q[i];
+                for (uint32_t i = tid; i < len; i += kLargeThreads)
+                    if (IMM_IN_BOUNDS(s_pos + i, b.big_cap, err, kChkBig)) out[i] = q[i];
             }
         }
         __syncthreads();
@@ -705,7 +714,7 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         if (!stop) {
             if (len == kLtCap) {
                 const uint32_t qi = atomicAdd(&b.sc->large_count, 1u);
-                b.large_q[qi] = rel;
+                if (IMM_IN_BOUNDS(qi, b.count, b.sc->bounds, kChkLargeQ)) b.large_q[qi] = rel;
                 b.set_len[rel] = kLenPending;
                 busy = false;
             } else {
@@ -719,7 +728,8 @@ lt_small_kernel(DevGraph g, SampleBatch b)
             b.set_edges[rel] = len;
             uint64_t pos = 0;
             if (reserve_small(b, rel, len, &pos))
-                for (uint32_t i = 0; i < len; ++i) b.stage[pos + i] = path[i][tid];
+                for (uint32_t i = 0; i < len; ++i)
+                    if (IMM_IN_BOUNDS(pos + i, b.stage_cap, b.sc->bounds, kChkStage)) b.stage[pos + i] = path[i][tid];
             busy = false;
         }
     }
@@ -773,6 +783,7 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                 const uint32_t bit = 1u << (u & 31);
                 if (bm[u >> 5] & bit) break;
                 bm[u >> 5] |= bit;
+                if (!IMM_IN_BOUNDS(len, ls.queue_cap, b.sc->bounds, kChkSlotQueue)) break;
                 q[len++] = u;
                 v = u;
                 lo = ulo;
@@ -791,9 +802,12 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
         if (ok) {
             uint32_t* out = b.big + pos;
             if (kind)
-                for (uint32_t i = lane; i < words; i += 32) out[i] = bm[i];
+                for (uint32_t i = lane; i < words; i += 32) {
+                    if (IMM_IN_BOUNDS(pos + i, b.big_cap, b.sc->bounds, kChkBig)) out[i] = bm[i];
+                }
             else
-                for (uint32_t i = lane; i < len; i += 32) out[i] = q[i];
+                for (uint32_t i = lane; i < len; i += 32)
+                    if (IMM_IN_BOUNDS(pos + i, b.big_cap, b.sc->bounds, kChkBig)) out[i] = q[i];
         }
         __syncwarp();
         for (uint32_t i = lane; i < len; i += 32) bm[q[i] >> 5] = 0;
@@ -1022,7 +1036,7 @@ compact_kernel(SampleBatch b, BatchOut ob, uint64_t committed, uint32_t* hist)
             const uint64_t D = shfl64(dst, o);
             for (uint32_t i = lane; i < L; i += 32) {
                 const uint32_t u = S[i];
-                ob.arena[D + i] = u;
+                if (IMM_IN_BOUNDS(D + i, ob.arena_cap, ob.bounds, kChkArena)) ob.arena[D + i] = u;
                 atomicAdd(&hist[u], 1u);
             }
         }
@@ -1043,7 +1057,7 @@ compact_kernel(SampleBatch b, BatchOut ob, uint64_t committed, uint32_t* hist)
             const uint32_t ex = __shfl_sync(kFull, excl, o);
             if (j < total) {
                 const uint32_t u = S[j - ex];
-                ob.arena[D + (j - ex)] = u;
+                if (IMM_IN_BOUNDS(D + (j - ex), ob.arena_cap, ob.bounds, kChkArena)) ob.arena[D + (j - ex)] = u;
                 atomicAdd(&hist[u], 1u);
             }
         }
@@ -1223,7 +1237,8 @@ cudaError_t launch_vertex_scan(const uint32_t* hist, uint32_t n, uint64_t* voff,
 // ===========================================================================
 __global__ void __launch_bounds__(256)
 index_scatter_kernel(uint64_t set_begin, uint64_t set_end, const uint64_t* off, const uint32_t* arena,
-                     const uint64_t* voff, uint32_t* cursor, uint32_t* inv)
+                     const uint64_t* voff, uint32_t* cursor, uint32_t* inv, uint64_t inv_cap,
+                     unsigned long long* err)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1246,7 +1261,8 @@ index_scatter_kernel(uint64_t set_begin, uint64_t set_end, const uint64_t* off, 
             const uint32_t sid = (uint32_t)(first + o);
             for (uint32_t i = lane; i < L; i += 32) {
                 const uint32_t u = arena[A + i];
-                inv[voff[u] + atomicAdd(&cursor[u], 1u)] = sid;
+                const uint64_t at = voff[u] + atomicAdd(&cursor[u], 1u);
+                if (IMM_IN_BOUNDS(at, inv_cap, err, kChkInv)) inv[at] = sid;
             }
         }
         const uint32_t sl = big ? 0u : len;
@@ -1265,22 +1281,24 @@ index_scatter_kernel(uint64_t set_begin, uint64_t set_end, const uint64_t* off, 
             const uint32_t ex = __shfl_sync(kFull, excl, o);
             if (j < total) {
                 const uint32_t u = arena[A + (j - ex)];
-                inv[voff[u] + atomicAdd(&cursor[u], 1u)] = (uint32_t)(first + o);
+                const uint64_t at = voff[u] + atomicAdd(&cursor[u], 1u);
+                if (IMM_IN_BOUNDS(at, inv_cap, err, kChkInv)) inv[at] = (uint32_t)(first + o);
             }
         }
     }
 }
 
 cudaError_t launch_index_scatter(uint64_t set_begin, uint64_t set_end, const uint64_t* off, const uint32_t* arena,
-                                 const uint64_t* voff, uint32_t* cursor, uint32_t* inv, const DeviceInfo& di,
-                                 cudaStream_t st)
+                                 const uint64_t* voff, uint32_t* cursor, uint32_t* inv, uint64_t inv_cap,
+                                 unsigned long long* err, const DeviceInfo& di, cudaStream_t st)
 {
     if (set_end <= set_begin) return cudaSuccess;
     const uint64_t warps = (set_end - set_begin + 31) / 32;
     uint64_t blocks = (warps + 7) / 8;
     const uint64_t cap = (uint64_t)di.sms * 16;
     if (blocks > cap) blocks = cap;
-    index_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(set_begin, set_end, off, arena, voff, cursor, inv);
+    index_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(set_begin, set_end, off, arena, voff, cursor, inv, inv_cap,
+                                                           err);
     return cudaGetLastError();
 }
 

@@ -147,7 +147,7 @@ cover_kernel(SelectState s, uint32_t j)
             if (!s.covered[sid]) {
                 s.covered[sid] = 1;
                 const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
-                s.newly[p] = sid;
+                if (IMM_IN_BOUNDS(p, s.nsets, s.bounds, kChkNewly)) s.newly[p] = sid;
                 vol += s.off[(uint64_t)sid + 1] - s.off[sid];
             }
         }
@@ -163,7 +163,7 @@ cover_kernel(SelectState s, uint32_t j)
         if (!s.covered[sid] && (s.bmp[b * s.words + wv] & bit)) {
             s.covered[sid] = 1;
             const unsigned long long p = atomicAdd(&s.newly_n[j], 1ull);
-            s.newly[p] = sid;
+            if (IMM_IN_BOUNDS(p, s.nsets, s.bounds, kChkNewly)) s.newly[p] = sid;
             vol += s.bmp_len[b];
             ++nb;
         }
@@ -410,7 +410,8 @@ __device__ void team_build_cand(const SelectState& s, uint32_t tau, Team t)
         uint32_t base = 0;
         if ((int)lane == leader) base = atomicAdd(s.cstate, (uint32_t)__popc(bal));
         base = __shfl_sync(kFull, base, leader);
-        if (take) s.cand[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)v;
+        const uint64_t at = base + __popc(bal & ((1u << lane) - 1u));
+        if (take && IMM_IN_BOUNDS(at, s.n, s.bounds, kChkCand)) s.cand[at] = (uint32_t)v;
     }
 }
 
@@ -425,7 +426,8 @@ __device__ __forceinline__ void append_newly(const SelectState& s, uint32_t j, b
     unsigned long long base = 0;
     if (lane == leader) base = atomicAdd(&s.newly_n[j], (unsigned long long)__popc(bal));
     base = __shfl_sync(kFull, base, leader);
-    if (take) s.newly[base + __popc(bal & ((1u << lane) - 1u))] = sid;
+    const uint64_t at = base + __popc(bal & ((1u << lane) - 1u));
+    if (take && IMM_IN_BOUNDS(at, s.nsets, s.bounds, kChkNewly)) s.newly[at] = sid;
 }
 
 template <class Team>
@@ -627,7 +629,8 @@ __device__ void team_gather_uncovered(const SelectState& s, uint32_t j, Team t)
         unsigned long long base = 0;
         if ((int)lane == leader) base = atomicAdd(&s.ubmp_n[j], (unsigned long long)__popc(bal));
         base = __shfl_sync(kFull, base, leader);
-        if (take) s.ubmp[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)b;
+        const uint64_t at = base + __popc(bal & ((1u << lane) - 1u));
+        if (take && IMM_IN_BOUNDS(at, s.nbmp, s.bounds, kChkUbmp)) s.ubmp[at] = (uint32_t)b;
     }
 }
 

@@ -132,7 +132,8 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB_PATH
+    # IMM_LIBRARY_VARIANT=bounds (tests) loads the bounds-checked build
+    path = _build.BOUNDS_LIB_PATH if os.environ.get("IMM_LIBRARY_VARIANT") == "bounds" else _build.LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: the CUDA library must be built (__graft_entry__.build()); "
                            "there is no CPU fallback")
@@ -150,6 +151,7 @@ def _load():
         "imm_run_ex": ([vp, i32, u32, f64, f64, u64, u32, vp, ctypes.POINTER(imm_stats)], i32),
         "imm_run_opim": ([vp, i32, u32, f64, f64, u64, vp, ctypes.POINTER(imm_opim_stats)], i32),
         "imm_set_tuning": ([vp, ctypes.POINTER(imm_tuning)], i32),
+        "imm_build_flags": ([], i32),
         "imm_get_tuning": ([vp, ctypes.POINTER(imm_tuning)], i32),
         "imm_autotune_batch": ([vp, u32, u32, ctypes.POINTER(imm_tuning), vp, vp], i32),
         "imm_reset_sets": ([vp], i32),
@@ -302,6 +304,13 @@ def imm_run_opim(ctx: _Ctx, model: int, k: int, epsilon: float, ell: float, rng_
     _check(ctx, _load().imm_run_opim(ctx.handle, model, k, epsilon, ell, rng_seed, seeds.ctypes.data,
                                      ctypes.byref(st)))
     return seeds[:k], st
+
+
+IMM_BUILD_BOUNDS_CHECK = 1
+
+
+def imm_build_flags() -> int:
+    return int(_load().imm_build_flags())
 
 
 def imm_set_tuning(ctx: _Ctx, **knobs) -> None:

@@ -68,3 +68,12 @@ def test_product_package_does_not_import_oracle():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "oracle.c" not in text, fn
+
+
+def test_bounds_checked_variant_exports_every_symbol():
+    from paper_2411_09473_gb300 import _build
+    plain = ctypes.CDLL(_build.build())
+    checked = ctypes.CDLL(_build.build(variant="bounds"))
+    missing = [n for n in _declared() if not hasattr(checked, n)]
+    assert not missing, missing
+    assert plain.imm_build_flags() == 0 and checked.imm_build_flags() == 1
