@@ -519,8 +519,10 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     // windows of 32 small quads per level: a vertex has at most (indeg + 6) / 4 quads
     const uint64_t wcap = (c->m + 6 * n) / 128 + 2;
     const uint64_t o_fn = up(n * 8), o_lq = o_fn + up(n * 8), o_lpre = o_lq + up(n * 16);
+    // chunks of one level: sum over its large vertices of ceil(quads / 64)
+    const uint64_t ccap = c->m / 256 + 2 * hcap + 64;
     const uint64_t o_wst = o_lpre + up(n * 4), o_hb = o_wst + up(wcap * 4);
-    const uint64_t o_he = o_hb + up(hcap * 4), slot = o_he + up(hcap * 16);
+    const uint64_t o_he = o_hb + up(hcap * 4), o_co = o_he + up(hcap * 16), slot = o_co + up(ccap * 4);
     const uint64_t o_ct = kGroupSlots * slot;
     const uint64_t bytes = o_ct + up(kGroupSlots * sizeof(GroupCounters));
     char* p;
@@ -538,6 +540,8 @@ int ensure_group(imm_ctx* c, GroupScratch* gs)
     gs->wst = reinterpret_cast<uint32_t*>(p + o_wst);
     gs->hb = reinterpret_cast<uint32_t*>(p + o_hb);
     gs->he = reinterpret_cast<uint4*>(p + o_he);
+    gs->cown = reinterpret_cast<uint32_t*>(p + o_co);
+    gs->ccap = (uint32_t)ccap;
     gs->stride = slot;
     gs->ctr = reinterpret_cast<GroupCounters*>(p + o_ct);
     gs->wcap = (uint32_t)wcap;

@@ -305,9 +305,11 @@ struct GroupScratch {
     uint32_t* wst;            // [wcap] first small entry of each 32-quad window
     uint32_t* hb;             // [hcap] first chunk of each large vertex of the level
     uint4* he;                // [hcap] large vertices: (rs, re, F lo, F hi)
+    uint32_t* cown;           // [ccap] large-list entry owning each chunk of the level
     uint64_t stride;          // bytes from each slot's arrays to the next slot's
     GroupCounters* ctr;       // [kGroupSlots], one per slot (ctr[0].claim serves all)
     uint32_t wcap, hcap;      // entries of wst and of hb / he
+    uint32_t ccap;            // entries of cown
     uint32_t lcap;            // entries of lq / lpre (n)
     unsigned long long* bounds;  // checked builds: the batch's error word
 };

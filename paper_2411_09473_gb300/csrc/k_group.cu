@@ -30,8 +30,8 @@
 // from one counter.  Expansion items are windows of 32 of the small
 // vertices' quads, one quad per lane (its owner found from per-warp run
 // records in shared memory), and 64-quad chunks of the large vertices, two
-// quads per lane sharing each set's bookkeeping (owner found by a 32-way
-// search over the chunk prefix).
+// quads per lane sharing each set's bookkeeping (owner read from a per-chunk
+// table the scan step writes).
 //
 // When no vertex is listed, two dense passes over vis give every set its
 // size and in-edge sum, reserve its output (member list, or an n-bit bitmap
@@ -62,7 +62,6 @@ constexpr uint32_t kChunkQuads = 64;   // quads of a large vertex per work item 
 // packed list counters: entries << 36 | quads (small list) or chunks (large list)
 constexpr int kPackShift = 36;
 constexpr unsigned long long kPackLow = (1ull << kPackShift) - 1;
-constexpr uint32_t kHeavySmem = 4096;  // chunk prefix entries per slot searched in shared memory
 
 __device__ __forceinline__ uint32_t lanemask_le_g()
 {
@@ -257,10 +256,10 @@ __device__ __forceinline__ void visit_quad(unsigned long long* fn, const QuadLiv
 struct SlotArrays {
     unsigned long long *vis, *fn;
     uint4 *lq, *he;
-    uint32_t *lpre, *wst, *hb;
+    uint32_t *lpre, *wst, *hb, *cown;
     GroupCounters* ct;
-    uint32_t lcap, wcap, hcap;  // entries of lq / lpre, wst, hb / he
-    unsigned long long* err;    // checked builds: the batch's error word
+    uint32_t lcap, wcap, hcap, ccap;  // entries of lq / lpre, wst, hb / he, cown
+    unsigned long long* err;          // checked builds: the batch's error word
 };
 
 __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32_t k)
@@ -275,10 +274,12 @@ __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32
     a.lpre = at(gs.lpre);
     a.wst = at(gs.wst);
     a.hb = at(gs.hb);
+    a.cown = at(gs.cown);
     a.ct = gs.ctr + k;
     a.lcap = gs.lcap;
     a.wcap = gs.wcap;
     a.hcap = gs.hcap;
+    a.ccap = gs.ccap;
     a.err = gs.bounds;
     return a;
 }
@@ -288,12 +289,16 @@ __device__ __forceinline__ SlotArrays slot_arrays(const GroupScratch& gs, uint32
 __device__ __forceinline__ void list_large(const SlotArrays& a, uint32_t par, uint32_t rs, uint32_t re,
                                            uint32_t nq, unsigned long long F)
 {
-    const unsigned long long old =
-        atomicAdd(&a.ct->hpack[par], (1ull << kPackShift) | (unsigned long long)((nq + kChunkQuads - 1) / kChunkQuads));
+    const uint32_t nch = (nq + kChunkQuads - 1) / kChunkQuads;
+    const unsigned long long old = atomicAdd(&a.ct->hpack[par], (1ull << kPackShift) | (unsigned long long)nch);
     const uint32_t i = (uint32_t)(old >> kPackShift);
     if (!IMM_IN_BOUNDS(i, a.hcap, a.err, kChkGroupLarge)) return;
-    a.hb[i] = (uint32_t)(old & kPackLow);
+    const uint32_t first = (uint32_t)(old & kPackLow);
+    a.hb[i] = first;
     a.he[i] = make_uint4(rs, re, (uint32_t)F, (uint32_t)(F >> 32));
+    // the owner of each of its chunks, so a chunk item finds its vertex in one load
+    for (uint32_t c = 0; c < nch; ++c)
+        if (IMM_IN_BOUNDS(first + c, a.ccap, a.err, kChkGroupLarge)) a.cown[first + c] = i;
 }
 
 // Small-list entry i of a vertex with 1..31 in-edge quads at quad offset off
@@ -332,9 +337,18 @@ constexpr uint32_t kSlotOffset = 2;       // steps by which slot k starts after 
 __device__ __forceinline__ void scan_item(const DevGraph& g, const SlotArrays& a, uint32_t par, uint32_t v0,
                                           uint32_t lane)
 {
-    for (uint32_t r = 0; r < kScanPerItem; r += 32) {
+    // the item's fn words are loaded at once (one round trip, not eight)
+    unsigned long long Fs[kScanPerItem / 32];
+#pragma unroll
+    for (uint32_t r = 0; r < kScanPerItem / 32; ++r) {
+        const uint32_t v = v0 + r * 32 + lane;
+        Fs[r] = v < g.n ? __ldcg(a.fn + v) : 0ull;
+    }
+#pragma unroll
+    for (uint32_t r8 = 0; r8 < kScanPerItem / 32; ++r8) {
+        const uint32_t r = r8 * 32;
         const uint32_t v = v0 + r + lane;
-        unsigned long long F = v < g.n ? __ldcg(a.fn + v) : 0ull;
+        unsigned long long F = Fs[r8];
         if (!__any_sync(kFull, F != 0ull)) continue;
         if (F) {
             __stcg(a.fn + v, 0ull);
@@ -373,24 +387,14 @@ __device__ __forceinline__ void scan_item(const DevGraph& g, const SlotArrays& a
 }
 
 // 64-quad chunk hc of the level's large vertices: lane t sweeps quads t and
-// t + 32 of the chunk (the second only when some lane has one there).
-// Owner: the last lo with hb[lo] <= hc (invariant hb[lo] <= hc < hb[lo +
-// span]; lane 0 probes lo itself, so the ballot is never empty).
+// t + 32 of the chunk (the second only when some lane has one there).  Its
+// vertex is the large-list entry the scan step recorded as its owner.
 __device__ __forceinline__ void large_item(const DevGraph& g, const PhiloxKeys& rk, const PhiloxSet* ps,
-                                           const SlotArrays& a, const uint32_t* s_hb, bool hsm, uint32_t nh,
-                                           uint32_t hc, uint32_t lane)
+                                           const SlotArrays& a, uint32_t hc, uint32_t lane)
 {
-    uint32_t lo = 0, span = nh;
-    while (span > 1) {
-        const uint32_t step = (span + 31) >> 5;
-        const uint32_t off = lane * step;
-        const bool le = off < span && (hsm ? s_hb[lo + off] : __ldcg(a.hb + lo + off)) <= hc;
-        const uint32_t t = 31 - __clz(__ballot_sync(kFull, le));
-        lo += t * step;
-        span = min(step, span - t * step);
-    }
+    const uint32_t lo = __ldcg(a.cown + hc);
     const uint4 e = __ldcg(a.he + lo);
-    const uint32_t first = hsm ? s_hb[lo] : __ldcg(a.hb + lo);
+    const uint32_t first = __ldcg(a.hb + lo);
     const uint32_t qa = (e.x >> 2) + (hc - first) * kChunkQuads + lane, qb = qa + 32;
     const uint32_t qlast = (e.y - 1) >> 2;
     const unsigned long long F = ((unsigned long long)e.w << 32) | e.z;
@@ -519,7 +523,6 @@ __device__ __forceinline__ void write_item(const DevGraph& g, const SampleBatch&
 __global__ void __launch_bounds__(kGroupThreads, kGroupBlocks)
 ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
 {
-    extern __shared__ uint32_t s_hbase[];  // [kGroupSlots][kHeavySmem] copies of the levels' chunk prefixes
     __shared__ PhiloxSet s_ps[kGroupSlots][kGroupSets];
     __shared__ uint4 s_rec[kGroupWarps][32];                // run records: rs, re, first slot
     __shared__ unsigned long long s_recF[kGroupWarps][32];  // run records: new bits
@@ -662,8 +665,6 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
                     a.ct->hpack[np] = 0;
                     a.ct->lpack[np] = 0;
                 }
-                if (v.nh <= kHeavySmem)
-                    for (uint32_t i = tid; i < v.nh; i += kGroupThreads) s_hbase[k * kHeavySmem + i] = __ldcg(a.hb + i);
             } else if (v.phase == kCount) {
                 if (tid < kGroupSets) {
                     s_cnt[k][tid] = 0;
@@ -693,12 +694,18 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
         // every slot first, then the large-vertex chunks (they even out the end)
         const uint32_t total = s_sbase[kGroupSlots];
         uint32_t* cl = claim + step % 3;
-        uint32_t c = 0;
-        if (lane == 0) c = atomicAdd(cl, 1u);
-        c = __shfl_sync(kFull, c, 0);
-        while (c < total) {
-            uint32_t cn = 0;  // the next claim, in flight while this item runs
-            if (lane == 0) cn = atomicAdd(cl, 1u);
+        // a claim takes two items while many remain (half the traffic on the
+        // one counter), one item near the end of the step (a shorter tail)
+        const uint32_t pair_until = total > 8u * kGroupWarps * gridDim.x ? total - 8u * kGroupWarps * gridDim.x : 0u;
+        uint32_t c0 = 0, take = pair_until ? 2u : 1u;
+        if (lane == 0) c0 = atomicAdd(cl, take);
+        c0 = __shfl_sync(kFull, c0, 0);
+        while (c0 < total) {
+            const uint32_t c1 = min(c0 + take, total);
+            take = c1 < pair_until ? 2u : 1u;
+            uint32_t cn = 0;  // the next claim, in flight while these items run
+            if (lane == 0) cn = atomicAdd(cl, take);
+          for (uint32_t c = c0; c < c1; ++c) {
             const bool lng = c < s_lbase[kGroupSlots];
             const uint32_t* base = lng ? s_lbase : s_sbase;
             uint32_t k = 0;
@@ -707,7 +714,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
             const SlotStep& v = s_st[k];
             const SlotArrays a = slot_arrays(gs, k);
             if (!lng) {
-                large_item(g, b.rk, s_ps[k], a, s_hbase + k * kHeavySmem, v.nh <= kHeavySmem, v.nh, ci, lane);
+                large_item(g, b.rk, s_ps[k], a, ci, lane);
             } else if (v.phase == kExpand) {
                 window_item(g, b.rk, s_ps[k], a, v.nl, v.nlq, ci, s_rec[wid], s_recF[wid], lane);
             } else if (v.phase == kScan) {
@@ -717,7 +724,8 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
             } else {
                 write_item(g, b, a, v.G, words, ci * kWordsPerItem, s_kind[k], s_pos[k], lane);
             }
-            c = __shfl_sync(kFull, cn, 0);
+          }
+            c0 = __shfl_sync(kFull, cn, 0);
         }
         __syncthreads();
         for (uint32_t k = 0; k < kGroupSlots; ++k) {
@@ -731,7 +739,7 @@ ic_group_kernel(DevGraph g, SampleBatch b, GroupScratch gs)
     }
 }
 
-constexpr size_t kGroupDynSmem = (size_t)kGroupSlots * kHeavySmem * 4;
+constexpr size_t kGroupDynSmem = 0;
 
 int ic_group_supported(const DeviceInfo& di)
 {
