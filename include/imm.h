@@ -236,6 +236,9 @@ int imm_run_opim(imm_ctx* ctx, int model, uint32_t k, double epsilon, double ell
  *                     cluster, smaller ones on one CTA
  *   select_cand       nonzero: one-CTA and cluster selections scan a
  *                     candidate list in rounds where it is exact
+ *   solo_cluster      nonzero: solo selections above select_cta_max_n over
+ *                     streams without bitmap-stored sets run on one 8-CTA
+ *                     cluster instead of the cooperative grid (default 0)
  * Batch and server workers take the tuning of their graph's context. */
 typedef struct imm_tuning {
     uint32_t batch_sets;
@@ -243,6 +246,7 @@ typedef struct imm_tuning {
     uint32_t select_cta_max_n;
     uint32_t cluster_min_n;
     uint32_t select_cand;
+    uint32_t solo_cluster;
 } imm_tuning;
 /* Errors: EINVAL (ctx or tuning NULL, batch_sets < 256). */
 int imm_set_tuning(imm_ctx* ctx, const imm_tuning* tuning);

@@ -637,12 +637,21 @@ constexpr int kLtThreads = 64;  // path[kLtCap][kLtThreads] stays within static 
 // (in-degree below 127) u's range; otherwise a short scan and row reads.
 constexpr uint32_t kCthrMask = (1u << 25) - 1;
 
-__device__ __forceinline__ uint32_t lt_step(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r, uint32_t* u,
-                                            uint32_t* ulo, uint32_t* uhi)
+// The guide entry a walk step at a vertex with in-edges [lo, hi) and draw r
+// starts from (nothing to load for a vertex without in-edges).
+__device__ __forceinline__ uint4 lt_guide_load(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r)
+{
+    if (hi == lo) return make_uint4(hi, 0u, 0u, 0u);
+    return __ldg(g.guide + lo + (uint32_t)(((uint64_t)r * (hi - lo)) >> 24));
+}
+
+// The step itself, from that entry: the picked in-edge j (hi when none) and
+// its tail u with u's in-edge range.  Memory is read only when the entry's
+// candidate is not the pick or the tail's range is not in the entry.
+__device__ __forceinline__ uint32_t lt_resolve(const DevGraph& g, uint32_t lo, uint32_t hi, uint32_t r, uint4 e,
+                                               uint32_t* u, uint32_t* ulo, uint32_t* uhi)
 {
     if (hi == lo) return hi;
-    const uint32_t d = hi - lo;
-    const uint4 e = __ldg(g.guide + lo + (uint32_t)(((uint64_t)r * d) >> 24));
     uint32_t j = e.x;
     if (j < hi && r < (e.y & kCthrMask)) {
         *u = e.z;
@@ -673,6 +682,8 @@ lt_small_kernel(DevGraph g, SampleBatch b)
     const uint32_t ltm = lanemask_lt();
     bool busy = false, done = false;
     uint32_t rel = 0, len = 0, v = 0, lo = 0, hi = 0;  // walk position and its in-edge range
+    uint32_t dr = 0;                                   // the draw at v
+    uint4 e = make_uint4(0, 0, 0, 0);                  // its guide entry (loaded one step ahead)
     PhiloxSet ps{};
     for (;;) {
         const uint32_t need = __ballot_sync(kFull, !busy && !done);
@@ -690,6 +701,8 @@ lt_small_kernel(DevGraph g, SampleBatch b)
                     ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
                     v = draw_root(b.rk, s, g.n);
                     edge_range(g, v, lo, hi);
+                    dr = philox_x(v, ps, b.rk).x >> 8;
+                    e = lt_guide_load(g, lo, hi, dr);
                     path[0][tid] = v;
                     len = 1;
                 } else {
@@ -699,12 +712,17 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         }
         if (__all_sync(kFull, done)) break;
         if (!busy) continue;
-        // one step of the reverse walk at v (in-edges [lo, hi))
-        const uint4 w = philox_x(v, ps, b.rk);
+        // one step of the reverse walk at v (in-edges [lo, hi)); the next
+        // step's guide entry is loaded before the revisit test, which then
+        // runs while the load is in flight
         uint32_t u = 0, ulo = 0, uhi = 0;
-        const uint32_t pick = lt_step(g, lo, hi, w.x >> 8, &u, &ulo, &uhi);
+        const uint32_t pick = lt_resolve(g, lo, hi, dr, e, &u, &ulo, &uhi);
         bool stop = pick == hi;
+        uint32_t r2 = 0;
+        uint4 e2 = make_uint4(0, 0, 0, 0);
         if (!stop) {
+            r2 = philox_x(u, ps, b.rk).x >> 8;
+            e2 = lt_guide_load(g, ulo, uhi, r2);
             for (uint32_t i = 0; i < len; ++i)
                 if (path[i][tid] == u) {
                     stop = true;
@@ -723,6 +741,8 @@ lt_small_kernel(DevGraph g, SampleBatch b)
                 v = u;
                 lo = ulo;
                 hi = uhi;
+                dr = r2;
+                e = e2;
             }
         } else {
             b.set_edges[rel] = len;
@@ -769,25 +789,33 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
         uint32_t len = 0;
         if (lane == 0) {
             const PhiloxSet ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
-            uint32_t v = draw_root(b.rk, s, g.n);
+            const uint32_t v = draw_root(b.rk, s, g.n);
             uint32_t lo, hi;
             edge_range(g, v, lo, hi);
             q[0] = v;
             bm[v >> 5] |= 1u << (v & 31);
             len = 1;
+            uint32_t r = philox_x(v, ps, b.rk).x >> 8;
+            uint4 e = lt_guide_load(g, lo, hi, r);
             for (;;) {
-                const uint4 w = philox_x(v, ps, b.rk);
                 uint32_t u = 0, ulo = 0, uhi = 0;
-                const uint32_t pick = lt_step(g, lo, hi, w.x >> 8, &u, &ulo, &uhi);
+                const uint32_t pick = lt_resolve(g, lo, hi, r, e, &u, &ulo, &uhi);
                 if (pick == hi) break;
+                // the visited word and the next step's guide entry (loaded on
+                // the chance that u is new) are in flight together: one round
+                // trip per step
                 const uint32_t bit = 1u << (u & 31);
-                if (bm[u >> 5] & bit) break;
-                bm[u >> 5] |= bit;
+                const uint32_t word = bm[u >> 5];
+                const uint32_t r2 = philox_x(u, ps, b.rk).x >> 8;
+                const uint4 e2 = lt_guide_load(g, ulo, uhi, r2);
+                if (word & bit) break;
+                bm[u >> 5] = word | bit;
                 if (!IMM_IN_BOUNDS(len, ls.queue_cap, b.sc->bounds, kChkSlotQueue)) break;
                 q[len++] = u;
-                v = u;
                 lo = ulo;
                 hi = uhi;
+                r = r2;
+                e = e2;
             }
             b.set_edges[rel] = len;
         }

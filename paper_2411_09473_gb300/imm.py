@@ -89,7 +89,7 @@ IMM_OPIM_KEY = 0xD1B54A32D192ED03
 class imm_tuning(ctypes.Structure):
     _fields_ = [("batch_sets", ctypes.c_uint32), ("group_min_mean", ctypes.c_uint32),
                 ("select_cta_max_n", ctypes.c_uint32), ("cluster_min_n", ctypes.c_uint32),
-                ("select_cand", ctypes.c_uint32)]
+                ("select_cand", ctypes.c_uint32), ("solo_cluster", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
