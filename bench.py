@@ -56,7 +56,7 @@ METRIC = "IMM seconds-to-seeds"
 ALU_OPS_PER_QUAD_EVAL = 44
 # DRAM bytes per quad evaluation of the dominant IC kernel on the 1M-vertex
 # workload, from one ncu capture (profiles/ic_group_kernel__ic_u01_1m_first20000sets.md)
-IC_DRAM_BYTES_PER_QUAD_EVAL = 38.357199e9 / 12215037853
+IC_DRAM_BYTES_PER_QUAD_EVAL = 32.628760e9 / 12215037853
 WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "ic_u1_256k", "batch64", "served")
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
