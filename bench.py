@@ -454,7 +454,7 @@ def run_plain(args, dist: Dist, name: str, steps: int, warmup: int, e2e_on: bool
         algo_bytes = 8.0 * edges + 16.0 * members
         achieved = algo_bytes / (ms_sample / 1e3) / 1e9 if ms_sample > 0 else 0.0
         peak, peak_kind = measured_peaks()
-        roof = {"kernel": "RRR sampling (LT): lt_small_kernel + lt_long_kernel", "bound": "hbm",
+        roof = {"kernel": "RRR sampling (LT): lt_small_kernel + lt_mid_kernel + lt_long_kernel", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind, "traffic": None,
                 "algorithmic_bytes": "8 B per walk step + 16 B per member",

@@ -104,7 +104,7 @@ struct imm_ctx {
     uint64_t index_bytes = 0;
 
     // sampling scratch
-    DBuf set_len, set_pos, set_edges, set_kind, large_q, bmp_rel;
+    DBuf set_len, set_pos, set_edges, set_kind, large_q, long_q, bmp_rel;
     uint32_t batch_cap = 0;
     DBuf stage;
     uint64_t stage_cap = 0;
@@ -114,8 +114,9 @@ struct imm_ctx {
     DBuf scan_tmp;
     DBuf slot_q, slot_bm;
     DBuf grp;  // grouped IC large path: masks, frontier lists, large-vertex list, counters
-    uint32_t nslots = 0;
-    uint64_t slot_words = 0;
+    DBuf mid;  // LT walks with per-walk tables (tables zero between launches)
+    uint32_t nslots = 0, mid_slots = 0;
+    uint64_t slot_words = 0, slot_qcap = 0;
     DBuf hist, cursor, vtmp;
 
     // selection scratch
@@ -129,6 +130,7 @@ struct imm_ctx {
     uint32_t next_batch = 1u << 22;  // reset to tune.batch_sets with the stream
     double avg_len = 0.0;
     double small_mean = 0.0;  // running mean members per small-path set
+    double lt_cont = 0.0;     // LT: fraction of the last batch's walks past the lane path
     double large_mean = 0.0;  // running mean members per large-path set
 
     // accounting for imm_stats
@@ -143,6 +145,7 @@ struct imm_ctx {
     uint32_t fb_large = 0;
     struct Pinned {
         uint32_t large_count;
+        uint32_t long_count;
         uint32_t k;
         BatchScalars sc;
         SelectState state;
@@ -329,6 +332,7 @@ void drop_stream(imm_ctx* c)
     c->avg_len = 0.0;
     c->small_mean = 0.0;
     c->large_mean = 0.0;
+    c->lt_cont = 0.0;
     c->next_batch = c->tune.batch_sets;
     if (c->off.p) cudaMemsetAsync(c->off.p, 0, sizeof(uint64_t), c->stream);
     if (c->cnt.p) cudaMemsetAsync(c->cnt.p, 0, (size_t)c->n * 4, c->stream);
@@ -357,7 +361,10 @@ void free_graph(imm_ctx* c)
     dfree(c, c->slot_q);
     dfree(c, c->slot_bm);
     dfree(c, c->grp);
+    dfree(c, c->mid);
     c->nslots = 0;
+    c->slot_qcap = 0;
+    c->mid_slots = 0;
     c->loaded = false;
 }
 
@@ -449,18 +456,46 @@ int load_graph_common(imm_ctx* c, uint32_t n, uint64_t m, const void* row, const
     return IMM_OK;
 }
 
-int ensure_slots(imm_ctx* c, uint32_t want_slots, bool need_bitmap)
+// Per-CTA slots of the large-set paths: a member queue of qcap entries and,
+// when asked for, an n-bit bitmap (zero between launches).
+int ensure_slots(imm_ctx* c, uint32_t want_slots, bool need_bitmap, uint64_t qcap)
 {
     const uint64_t words = ((uint64_t)c->n + 31) / 32;
-    if (c->nslots >= want_slots && (!need_bitmap || c->slot_bm.bytes >= (size_t)want_slots * words * 4))
+    if (c->nslots >= want_slots && c->slot_qcap >= qcap &&
+        (!need_bitmap || c->slot_bm.bytes >= (size_t)want_slots * words * 4))
         return IMM_OK;
-    TRY(dalloc(c, c->slot_q, (size_t)want_slots * c->n * 4));
+    want_slots = std::max(want_slots, c->nslots);
+    qcap = std::max(qcap, c->slot_qcap);
+    c->nslots = 0;  // nothing usable until both are allocated
+    c->slot_qcap = 0;
+    TRY(dalloc(c, c->slot_q, (size_t)want_slots * qcap * 4));
     if (need_bitmap) {
         TRY(dalloc(c, c->slot_bm, (size_t)want_slots * words * 4));
         CK(cudaMemsetAsync(c->slot_bm.p, 0, (size_t)want_slots * words * 4, c->stream));
     }
     c->nslots = want_slots;
+    c->slot_qcap = qcap;
     c->slot_words = words;
+    return IMM_OK;
+}
+
+// Per-walk tables of the LT walks past the lane path (zeroed once; every
+// walk clears the entries it set); ms covers all of them.
+int ensure_mid(imm_ctx* c, uint32_t want_slots, MidSlots* ms)
+{
+    const size_t per = (size_t)(kLtMidHash + 2 * kLtMidCap) * 4;
+    if (c->mid_slots < want_slots) {
+        const uint32_t cap = std::min<uint32_t>((want_slots + 1023u) / 1024u * 1024u, kLtMidSlotsMax);
+        c->mid_slots = 0;
+        TRY(dalloc(c, c->mid, (size_t)cap * per));
+        CK(cudaMemsetAsync(c->mid.p, 0, (size_t)cap * per, c->stream));
+        c->mid_slots = cap;
+    }
+    uint32_t* base = P<uint32_t>(c->mid);
+    ms->tab = base;
+    ms->path = base + (size_t)c->mid_slots * kLtMidHash;
+    ms->hpos = ms->path + (size_t)c->mid_slots * kLtMidCap;
+    ms->nslots = c->mid_slots;
     return IMM_OK;
 }
 
@@ -667,6 +702,7 @@ int batch_phase1(imm_ctx* c, uint64_t theta)
         TRY(dalloc(c, c->set_edges, (size_t)cap * 4));
         TRY(dalloc(c, c->set_kind, (size_t)cap * 4));
         TRY(dalloc(c, c->large_q, (size_t)cap * 4));
+        TRY(dalloc(c, c->long_q, (size_t)cap * 4));
         TRY(dalloc(c, c->bmp_rel, (size_t)cap * 4));
         TRY(dalloc(c, c->scan_tmp, scan_tmp_words(cap) * 8));
         c->batch_cap = cap;
@@ -710,13 +746,24 @@ int batch_phase1(imm_ctx* c, uint64_t theta)
     b.big = P<uint32_t>(c->big);
     b.big_cap = 0;
     b.large_q = P<uint32_t>(c->large_q);
+    b.long_q = P<uint32_t>(c->long_q);
     b.sc = sc;
     const DevGraph g = dev_graph(c);
+    MidSlots ms{};
+    if (c->model == IMM_LT) {
+        // tables for the walks that outgrow the lane path, sized from the
+        // last batch's share of them (a walk that finds none left is sampled
+        // again by the per-walk-table kernel)
+        const double f = c->lt_cont > 0 ? c->lt_cont : 0.1;
+        const double want = std::min<double>((double)kLtMidSlotsMax, (double)count * f * 1.25 + 256.0);
+        TRY(ensure_mid(c, std::min<uint32_t>((uint32_t)want, count), &ms));
+    }
     CK(cudaEventRecord(c->ev[0], c->stream));
     if (c->model == IMM_IC) CK(launch_ic_small(g, b, c->di, c->stream));
-    else CK(launch_lt_small(g, b, c->di, c->stream));
+    else CK(launch_lt_small(g, b, ms, c->di, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
     CK(cudaMemcpyAsync(&c->pin->large_count, &sc->large_count, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&c->pin->long_count, &sc->long_count, 4, cudaMemcpyDeviceToHost, c->stream));
     c->acc_sample_launches += 1;
     c->acc_launches += 1;
     return IMM_OK;
@@ -727,15 +774,16 @@ int batch_phase2(imm_ctx* c)
     c->acc_sample_ms += elapsed(c, 0, 1);
     SampleBatch& b = c->fb;
     const uint32_t large_count = c->pin->large_count;
+    const uint32_t long_count = c->pin->long_count;  // LT walks already bound for the bitmap slots
     const uint32_t words = b.words;
-    c->fb_large = large_count;
-    if (large_count) {
+    c->fb_large = large_count + long_count;
+    if (large_count + long_count) {
         // outputs of the large path: a list or a bitmap of `words` words
         // each; capped by a memory budget (sets past the cap are resampled)
         const uint64_t fr = device_free_bytes() + c->big.bytes;
         const uint64_t budget = std::max<uint64_t>((uint64_t)words * 4,
                                                    std::min<uint64_t>(fr / 4, 16ull << 30) / 4);
-        const uint64_t need = std::min<uint64_t>((uint64_t)large_count * words, budget);
+        const uint64_t need = std::min<uint64_t>((uint64_t)(large_count + long_count) * words, budget);
         if (c->big_cap < need) {
             TRY(ensure(c, c->big, need * 4));
             c->big_cap = c->big.bytes / 4;
@@ -756,22 +804,38 @@ int batch_phase2(imm_ctx* c)
             CK(cudaEventRecord(c->ev[3], c->stream));
         } else {
             const uint32_t want_slots = std::min<uint32_t>(
-                large_count, ic ? (uint32_t)c->di.sms : (uint32_t)std::min(c->di.sms * 2, 1024));
+                large_count + long_count, ic ? (uint32_t)c->di.sms : (uint32_t)std::min(c->di.sms * 2, 1024));
+            MidSlots ms{};
             if (ic) {
                 const bool smem = ic_large_uses_smem(c->n, c->di) != 0;
-                TRY(ensure_slots(c, want_slots, !smem));
+                TRY(ensure_slots(c, want_slots, !smem, c->n));
             } else {
-                TRY(ensure_slots(c, want_slots, true));
+                TRY(ensure_slots(c, want_slots, true, (uint64_t)words + 1));
+                if (large_count) {
+                    TRY(ensure_mid(c, std::min<uint32_t>(large_count, kLtMidSlotsMax), &ms));
+                    ms.nslots = std::min<uint32_t>(ms.nslots, large_count);
+                }
             }
             LargeSlots ls;
             ls.queues = P<uint32_t>(c->slot_q);
-            ls.queue_cap = c->n;
+            ls.queue_cap = c->slot_qcap;
             ls.bitmaps = P<uint32_t>(c->slot_bm);
             ls.bitmap_words = words;
-            ls.nslots = std::min<uint32_t>(c->nslots, large_count);
+            ls.nslots = std::min<uint32_t>(c->nslots, large_count + long_count);
             CK(cudaEventRecord(c->ev[2], c->stream));
-            if (ic) CK(launch_ic_large(g, b, ls, c->di, c->stream));
-            else CK(launch_lt_long(g, b, ls, c->di, c->stream));
+            if (ic) {
+                CK(launch_ic_large(g, b, ls, c->di, c->stream));
+            } else {
+                // walks the lane path handed back (its tables were used up)
+                // with per-walk tables; walks longer than a table or a list
+                // holds on the bitmap slots
+                if (large_count) {
+                    CK(launch_lt_mid(g, b, ms, c->stream));
+                    c->acc_sample_launches += 1;
+                    c->acc_launches += 1;
+                }
+                CK(launch_lt_long(g, b, ls, c->di, c->stream));
+            }
             CK(cudaEventRecord(c->ev[3], c->stream));
         }
         c->acc_sample_launches += 1;
@@ -878,6 +942,7 @@ int batch_phase3(imm_ctx* c, bool* progress)
         const double m = (double)hs.stage_cursor / (double)(count - c->fb_large);
         c->small_mean = c->small_mean > 0 ? std::max(m, 0.5 * (c->small_mean + m)) : m;
     }
+    if (c->model == IMM_LT) c->lt_cont = (double)hs.mid_claim / (double)count;
     if (c->fb_large && hs.all_members > hs.stage_cursor) {
         const double m = (double)(hs.all_members - hs.stage_cursor) / (double)c->fb_large;
         c->large_mean = c->large_mean > 0 ? 0.5 * (c->large_mean + m) : m;
@@ -1573,7 +1638,7 @@ void imm_destroy(imm_ctx* c)
     DeviceGuard guard(c->device);
     free_graph(c);
     DBuf* bufs[] = {&c->off,      &c->arena,   &c->set_len,  &c->set_pos, &c->set_edges, &c->set_kind,
-                    &c->large_q,  &c->bmp_rel, &c->stage,    &c->big,     &c->scalars,   &c->scan_tmp,
+                    &c->large_q,  &c->long_q,  &c->bmp_rel,  &c->stage,   &c->big,       &c->scalars,   &c->scan_tmp,
                     &c->covered,  &c->newly,   &c->keys,     &c->newly_n, &c->vol_cov,   &c->vol_list,
                     &c->bmp_cov,  &c->ubmp,    &c->ubmp_n,   &c->seeds,   &c->dsegs,     &c->flags,
                     &c->set_bmp,  &c->bmp,     &c->dstate,

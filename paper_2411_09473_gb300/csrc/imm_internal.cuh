@@ -155,6 +155,10 @@ struct BatchScalars {
     int error;
     int pad;
     unsigned long long bounds[3];     // checked builds: first failed index check (where, index, bound)
+    uint32_t long_count;    // LT: walks handed on to the bitmap path
+    uint32_t long_cursor;   // next entry of that queue
+    uint32_t mid_claim;     // LT: per-walk tables claimed by the lane path
+    uint32_t pad2;
 };
 
 // Index checks of the bounds-checked build (-DIMM_BOUNDS_CHECK): an index at
@@ -182,7 +186,7 @@ constexpr bool kBoundsChecked = false;
 // where codes of the checks
 enum : uint32_t {
     kChkStage = 1, kChkLargeQ, kChkSlotQueue, kChkSlotBitmap, kChkBig, kChkArena, kChkInv, kChkGroupSmall,
-    kChkGroupWin, kChkGroupLarge, kChkNewly, kChkCand, kChkUbmp, kChkCounts
+    kChkGroupWin, kChkGroupLarge, kChkNewly, kChkCand, kChkUbmp, kChkCounts, kChkLongQ
 };
 
 constexpr uint64_t kBigFlag = 1ull << 63;  // set_pos points into the large-output buffer
@@ -202,6 +206,7 @@ struct SampleBatch {
     uint32_t* big;        // large-set outputs
     uint64_t big_cap;
     uint32_t* large_q;    // [count] batch-relative ids for the large-set path
+    uint32_t* long_q;     // [count] LT: ids of walks too long for a per-walk table
     BatchScalars* sc;
 };
 
@@ -232,6 +237,24 @@ struct LargeSlots {
     uint64_t queue_cap;
     uint32_t* bitmaps;
     uint64_t bitmap_words;
+    uint32_t nslots;
+};
+
+// Per-walk tables of LT walks past the lane path's kLtCap members: an
+// open-addressing table of kLtMidHash entries (member + 1, 0 = empty; zero
+// between walks) in global memory, and the members it holds with their
+// table slots in walk order.  The lane path claims them for the walks it
+// continues (members kLtCap.. go to the table); the per-walk-table kernel
+// uses them for walks it samples whole.  A walk longer than kLtMidCap
+// members (or than a list of n/32 members) goes on to the bitmap path.
+constexpr uint32_t kLtMidHashBits = 11;
+constexpr uint32_t kLtMidHash = 1u << kLtMidHashBits;  // load factor at most 1/2
+constexpr uint32_t kLtMidCap = 1024;
+constexpr uint32_t kLtMidSlotsMax = 8192;  // 16 KB each
+struct MidSlots {
+    uint32_t* tab;   // [nslots][kLtMidHash]
+    uint32_t* path;  // [nslots][kLtMidCap]
+    uint32_t* hpos;  // [nslots][kLtMidCap]
     uint32_t nslots;
 };
 
@@ -279,7 +302,9 @@ int ic_large_uses_smem(uint32_t n, const DeviceInfo& di);
 cudaError_t launch_ic_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
 cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
                             const DeviceInfo& di, cudaStream_t st);
-cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st);
+cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const MidSlots& ms, const DeviceInfo& di,
+                            cudaStream_t st);
+cudaError_t launch_lt_mid(const DevGraph& g, const SampleBatch& b, const MidSlots& ms, cudaStream_t st);
 cudaError_t launch_lt_long(const DevGraph& g, const SampleBatch& b, const LargeSlots& ls,
                            const DeviceInfo& di, cudaStream_t st);
 // Grouped IC large path: the large sets of a batch, 64 at a time, as one

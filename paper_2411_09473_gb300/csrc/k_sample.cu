@@ -673,17 +673,45 @@ __device__ __forceinline__ uint32_t lt_resolve(const DevGraph& g, uint32_t lo, u
     return j;
 }
 
+// Walks that outgrow the lane's path go on in a per-walk table claimed from
+// the pool (MidSlots; the pool's tables are zero between walks): members
+// kLtCap.. are kept there, and a step's table probe is issued together with
+// the next guide entry.  A lane whose claim finds the pool used up hands the
+// walk to the per-walk-table kernel, which samples it again from its root.
+// A lane's path has a 1024-bit membership filter, so the path is scanned
+// only when the filter holds the vertex's bit (a revisit, or 1 in 7 steps at
+// most while the path fills).
+constexpr int kLtFiltWords = 32;
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t lt_mid_hash(uint32_t u)
+{
+    return (u * 0x9E3779B1u) >> (32 - kLtMidHashBits);
+}
+
+__device__ __forceinline__ uint32_t lt_filt_bit(uint32_t u)
+{
+    return (u * 0x85EBCA6Bu) >> 22;  // 10 bits
+}
+
 __global__ void __launch_bounds__(kLtThreads)
-lt_small_kernel(DevGraph g, SampleBatch b)
+lt_small_kernel(DevGraph g, SampleBatch b, MidSlots ms)
 {
     __shared__ uint32_t path[kLtCap][kLtThreads];
+    __shared__ uint32_t filt[kLtFiltWords][kLtThreads];
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31;
     const uint32_t ltm = lanemask_lt();
+    // total members a walk may reach here: a list of at most n/32 members
+    // and the table's capacity (no continuation when that is below kLtCap)
+    const uint32_t cap = b.words < kLtMidCap ? b.words : kLtMidCap;
+#pragma unroll
+    for (int w = 0; w < kLtFiltWords; ++w) filt[w][tid] = 0u;
     bool busy = false, done = false;
     uint32_t rel = 0, len = 0, v = 0, lo = 0, hi = 0;  // walk position and its in-edge range
     uint32_t dr = 0;                                   // the draw at v
     uint4 e = make_uint4(0, 0, 0, 0);                  // its guide entry (loaded one step ahead)
+    uint32_t slot = kNoSlot;                           // pool slot of a continued walk
     PhiloxSet ps{};
     for (;;) {
         const uint32_t need = __ballot_sync(kFull, !busy && !done);
@@ -704,6 +732,8 @@ lt_small_kernel(DevGraph g, SampleBatch b)
                     dr = philox_x(v, ps, b.rk).x >> 8;
                     e = lt_guide_load(g, lo, hi, dr);
                     path[0][tid] = v;
+                    const uint32_t fb = lt_filt_bit(v);
+                    filt[fb >> 5][tid] |= 1u << (fb & 31);
                     len = 1;
                 } else {
                     done = true;
@@ -712,50 +742,110 @@ lt_small_kernel(DevGraph g, SampleBatch b)
         }
         if (__all_sync(kFull, done)) break;
         if (!busy) continue;
+        uint32_t* tab = ms.tab + (slot != kNoSlot ? (uint64_t)slot * kLtMidHash : 0ull);
         // one step of the reverse walk at v (in-edges [lo, hi)); the next
-        // step's guide entry is loaded before the revisit test, which then
-        // runs while the load is in flight
+        // step's guide entry and the table probe are loaded before the
+        // revisit test on the path, which then runs while they are in flight
         uint32_t u = 0, ulo = 0, uhi = 0;
         const uint32_t pick = lt_resolve(g, lo, hi, dr, e, &u, &ulo, &uhi);
         bool stop = pick == hi;
-        uint32_t r2 = 0;
+        uint32_t r2 = 0, h = 0;
         uint4 e2 = make_uint4(0, 0, 0, 0);
         if (!stop) {
             r2 = philox_x(u, ps, b.rk).x >> 8;
             e2 = lt_guide_load(g, ulo, uhi, r2);
-            for (uint32_t i = 0; i < len; ++i)
-                if (path[i][tid] == u) {
-                    stop = true;
-                    break;
+            uint32_t t = 0;
+            if (slot != kNoSlot) {
+                h = lt_mid_hash(u);
+                t = tab[h];
+            }
+            const uint32_t fb = lt_filt_bit(u);
+            if (filt[fb >> 5][tid] & (1u << (fb & 31))) {
+                const uint32_t pl = len < kLtCap ? len : kLtCap;
+                for (uint32_t i = 0; i < pl; ++i)
+                    if (path[i][tid] == u) {
+                        stop = true;
+                        break;
+                    }
+            }
+            if (!stop && slot != kNoSlot) {
+                // linear probing ends: the table holds at most cap - kLtCap
+                // <= half its entries
+                while (t != 0u && t != u + 1u) {
+                    h = (h + 1u) & (kLtMidHash - 1u);
+                    t = tab[h];
                 }
+                stop = t != 0u;
+            }
         }
         if (!stop) {
-            if (len == kLtCap) {
-                const uint32_t qi = atomicAdd(&b.sc->large_count, 1u);
-                if (IMM_IN_BOUNDS(qi, b.count, b.sc->bounds, kChkLargeQ)) b.large_q[qi] = rel;
-                b.set_len[rel] = kLenPending;
-                busy = false;
-            } else {
+            bool keep = true;
+            if (len < kLtCap) {
                 path[len][tid] = u;
+                const uint32_t fb = lt_filt_bit(u);
+                filt[fb >> 5][tid] |= 1u << (fb & 31);
+            } else if (len == cap || (slot == kNoSlot && cap <= kLtCap)) {
+                // longer than a list or a table holds: the bitmap path
+                const uint32_t o = atomicAdd(&b.sc->long_count, 1u);
+                if (IMM_IN_BOUNDS(o, b.count, b.sc->bounds, kChkLongQ)) b.long_q[o] = rel;
+                b.set_len[rel] = kLenPending;
+                keep = false;
+            } else {
+                if (slot == kNoSlot) {
+                    const uint32_t sl = atomicAdd(&b.sc->mid_claim, 1u);
+                    if (sl < ms.nslots) {
+                        slot = sl;
+                        tab = ms.tab + (uint64_t)slot * kLtMidHash;
+                        h = lt_mid_hash(u);  // the table is empty
+                    } else {
+                        const uint32_t qi = atomicAdd(&b.sc->large_count, 1u);
+                        if (IMM_IN_BOUNDS(qi, b.count, b.sc->bounds, kChkLargeQ)) b.large_q[qi] = rel;
+                        b.set_len[rel] = kLenPending;
+                        keep = false;
+                    }
+                }
+                if (keep) {
+                    const uint64_t at = (uint64_t)slot * kLtMidCap + (len - kLtCap);
+                    tab[h] = u + 1u;
+                    ms.hpos[at] = h;
+                    ms.path[at] = u;
+                }
+            }
+            if (keep) {
                 ++len;
                 v = u;
                 lo = ulo;
                 hi = uhi;
                 dr = r2;
                 e = e2;
+                continue;
             }
         } else {
             b.set_edges[rel] = len;
             uint64_t pos = 0;
-            if (reserve_small(b, rel, len, &pos))
-                for (uint32_t i = 0; i < len; ++i)
+            if (reserve_small(b, rel, len, &pos)) {
+                const uint32_t pl = len < kLtCap ? len : kLtCap;
+                for (uint32_t i = 0; i < pl; ++i)
                     if (IMM_IN_BOUNDS(pos + i, b.stage_cap, b.sc->bounds, kChkStage)) b.stage[pos + i] = path[i][tid];
-            busy = false;
+                for (uint32_t i = pl; i < len; ++i)
+                    if (IMM_IN_BOUNDS(pos + i, b.stage_cap, b.sc->bounds, kChkStage))
+                        b.stage[pos + i] = ms.path[(uint64_t)slot * kLtMidCap + (i - kLtCap)];
+            }
         }
+        // the walk ends here (stored, or handed on): clear its table entries
+        // and its filter
+        if (slot != kNoSlot) {
+            for (uint32_t i = kLtCap; i < len; ++i) tab[ms.hpos[(uint64_t)slot * kLtMidCap + (i - kLtCap)]] = 0u;
+            slot = kNoSlot;
+        }
+#pragma unroll
+        for (int w = 0; w < kLtFiltWords; ++w) filt[w][tid] = 0u;
+        busy = false;
     }
 }
 
-cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const DeviceInfo& di, cudaStream_t st)
+cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const MidSlots& ms, const DeviceInfo& di,
+                            cudaStream_t st)
 {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lt_small_kernel, kLtThreads, 0);
@@ -764,12 +854,100 @@ cudaError_t launch_lt_small(const DevGraph& g, const SampleBatch& b, const Devic
     uint64_t grid = (uint64_t)di.sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     if (grid > want) grid = want;
     if (grid == 0) grid = 1;
-    lt_small_kernel<<<(unsigned)grid, kLtThreads, 0, st>>>(g, b);
+    lt_small_kernel<<<(unsigned)grid, kLtThreads, 0, st>>>(g, b, ms);
     return cudaGetLastError();
 }
 
 // ===========================================================================
-// LT, long walks: one thread per walk with an n-bit global bitmap slot.
+// LT, walks past the lane path's capacity: one thread per walk (every walk
+// of the batch at once, up to kLtMidSlotsMax), visited set in a per-walk
+// table.  Each step's table probe is issued together with the next step's
+// guide entry, so a step costs one memory round trip as on the other paths.
+// ===========================================================================
+constexpr int kLtMidThreads = 128;
+
+__global__ void __launch_bounds__(kLtMidThreads)
+lt_mid_kernel(DevGraph g, SampleBatch b, MidSlots ms)
+{
+    const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= ms.nslots) return;
+    uint32_t* tab = ms.tab + (uint64_t)slot * kLtMidHash;
+    uint32_t* path = ms.path + (uint64_t)slot * kLtMidCap;
+    uint32_t* hpos = ms.hpos + (uint64_t)slot * kLtMidCap;
+    const uint32_t large_count = b.sc->large_count;
+    // a walk longer than a list of n/32 members is stored as a bitmap: the
+    // bitmap path takes it
+    const uint32_t cap = b.words < kLtMidCap ? b.words : kLtMidCap;
+    for (uint32_t idx = slot; idx < large_count; idx += ms.nslots) {
+        const uint32_t rel = b.large_q[idx];
+        const uint64_t s = b.base + rel;
+        const PhiloxSet ps = philox_set((uint32_t)s, (uint32_t)(s >> 32), kTagLT, b.rk);
+        uint32_t v = draw_root(b.rk, s, g.n);
+        uint32_t lo, hi;
+        edge_range(g, v, lo, hi);
+        uint32_t h = lt_mid_hash(v);
+        tab[h] = v + 1;
+        hpos[0] = h;
+        path[0] = v;
+        uint32_t len = 1;
+        bool over = false;
+        uint32_t r = philox_x(v, ps, b.rk).x >> 8;
+        uint4 e = lt_guide_load(g, lo, hi, r);
+        for (;;) {
+            uint32_t u = 0, ulo = 0, uhi = 0;
+            const uint32_t pick = lt_resolve(g, lo, hi, r, e, &u, &ulo, &uhi);
+            if (pick == hi) break;
+            h = lt_mid_hash(u);
+            uint32_t t = tab[h];
+            const uint32_t r2 = philox_x(u, ps, b.rk).x >> 8;
+            const uint4 e2 = lt_guide_load(g, ulo, uhi, r2);
+            // linear probing ends: the table holds at most cap <= half its
+            // entries
+            while (t != 0u && t != u + 1u) {
+                h = (h + 1u) & (kLtMidHash - 1u);
+                t = tab[h];
+            }
+            if (t) break;  // u is on the walk already
+            if (len == cap) {
+                over = true;
+                break;
+            }
+            tab[h] = u + 1u;
+            hpos[len] = h;
+            path[len] = u;
+            ++len;
+            lo = ulo;
+            hi = uhi;
+            r = r2;
+            e = e2;
+        }
+        for (uint32_t i = 0; i < len; ++i) tab[hpos[i]] = 0u;
+        if (over) {
+            const uint32_t o = atomicAdd(&b.sc->long_count, 1u);
+            if (IMM_IN_BOUNDS(o, b.count, b.sc->bounds, kChkLongQ)) b.long_q[o] = rel;
+            continue;
+        }
+        b.set_edges[rel] = len;
+        uint64_t pos = 0;
+        if (reserve_big(b, rel, len, 0u, &pos)) {
+            uint32_t* out = b.big + pos;
+            for (uint32_t i = 0; i < len; ++i)
+                if (IMM_IN_BOUNDS(pos + i, b.big_cap, b.sc->bounds, kChkBig)) out[i] = path[i];
+        }
+    }
+}
+
+cudaError_t launch_lt_mid(const DevGraph& g, const SampleBatch& b, const MidSlots& ms, cudaStream_t st)
+{
+    const unsigned grid = (ms.nslots + kLtMidThreads - 1) / kLtMidThreads;
+    lt_mid_kernel<<<grid, kLtMidThreads, 0, st>>>(g, b, ms);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// LT, walks longer still: one thread per walk with an n-bit global bitmap
+// slot; the member queue holds the first n/32 + 1 members (a longer walk is
+// stored as the bitmap).
 // ===========================================================================
 __global__ void __launch_bounds__(32)
 lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
@@ -777,14 +955,14 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
     const int lane = threadIdx.x;
     uint32_t* bm = ls.bitmaps + (uint64_t)blockIdx.x * ls.bitmap_words;
     uint32_t* q = ls.queues + (uint64_t)blockIdx.x * ls.queue_cap;
-    const uint32_t large_count = b.sc->large_count;
+    const uint32_t long_count = b.sc->long_count;
     const uint32_t words = b.words;
     for (;;) {
         uint32_t idx = 0;
-        if (lane == 0) idx = atomicAdd(&b.sc->large_cursor, 1u);
+        if (lane == 0) idx = atomicAdd(&b.sc->long_cursor, 1u);
         idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= large_count) break;
-        const uint32_t rel = b.large_q[idx];
+        if (idx >= long_count) break;
+        const uint32_t rel = b.long_q[idx];
         const uint64_t s = b.base + rel;
         uint32_t len = 0;
         if (lane == 0) {
@@ -810,8 +988,8 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                 const uint4 e2 = lt_guide_load(g, ulo, uhi, r2);
                 if (word & bit) break;
                 bm[u >> 5] = word | bit;
-                if (!IMM_IN_BOUNDS(len, ls.queue_cap, b.sc->bounds, kChkSlotQueue)) break;
-                q[len++] = u;
+                if (len < ls.queue_cap) q[len] = u;
+                ++len;
                 lo = ulo;
                 hi = uhi;
                 r = r2;
@@ -838,7 +1016,10 @@ lt_long_kernel(DevGraph g, SampleBatch b, LargeSlots ls)
                     if (IMM_IN_BOUNDS(pos + i, b.big_cap, b.sc->bounds, kChkBig)) out[i] = q[i];
         }
         __syncwarp();
-        for (uint32_t i = lane; i < len; i += 32) bm[q[i] >> 5] = 0;
+        if (kind)
+            for (uint32_t i = lane; i < words; i += 32) bm[i] = 0;
+        else
+            for (uint32_t i = lane; i < len; i += 32) bm[q[i] >> 5] = 0;
         __syncwarp();
     }
 }

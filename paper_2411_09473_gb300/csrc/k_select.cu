@@ -31,6 +31,13 @@ __device__ __forceinline__ uint64_t shfl64s(uint64_t x, int srcLane)
     return ((uint64_t)hi << 32) | lo;
 }
 
+__device__ __forceinline__ uint64_t shfl64s_up(uint64_t x, int d)
+{
+    const uint32_t lo = __shfl_up_sync(kFull, (uint32_t)x, d);
+    const uint32_t hi = __shfl_up_sync(kFull, (uint32_t)(x >> 32), d);
+    return ((uint64_t)hi << 32) | lo;
+}
+
 __device__ __forceinline__ uint32_t owner_lane(uint32_t j, uint32_t incl)
 {
     uint32_t o = 0;
@@ -313,22 +320,35 @@ struct ClusterTeam {
 template <class Team>
 __device__ void team_argmax(const SelectState& s, uint32_t j, Team t, unsigned long long* s_red)
 {
-    // four vertices per step with 16-byte count loads (work is 256-byte
-    // aligned); the ragged tail one by one
+    // four vertices per load with 16-byte count loads (work is 256-byte
+    // aligned), eight loads issued before any is used (the counts sit in L2:
+    // the pass is bound by load latency, not bandwidth); the ragged tail one
+    // by one
+    constexpr int kU = 8;
     unsigned long long best = 0;
     const uint64_t n4 = s.n >> 2;
     const uint4* w4 = reinterpret_cast<const uint4*>(s.work);
     const uint32_t* p4 = reinterpret_cast<const uint32_t*>(s.picked);
-    for (uint64_t i = t.rank(); i < n4; i += t.size()) {
-        const uint4 w = w4[i];
-        const uint32_t pk = p4[i];
-        const uint32_t v = (uint32_t)(i << 2);
-        const uint32_t c[4] = {w.x, w.y, w.z, w.w};
+    const uint64_t stride = t.size();
+    for (uint64_t i0 = t.rank(); i0 < n4; i0 += kU * stride) {
+        uint4 w[kU];
+        uint32_t pk[kU];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!((pk >> (8 * q)) & 0xFFu)) {
-                const unsigned long long key = ((unsigned long long)c[q] << 32) | (0xFFFFFFFFu - (v + q));
-                best = key > best ? key : best;
+        for (int u = 0; u < kU; ++u) {
+            const uint64_t i = i0 + u * stride;
+            w[u] = i < n4 ? w4[i] : make_uint4(0u, 0u, 0u, 0u);
+            pk[u] = i < n4 ? p4[i] : 0x01010101u;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t v = (uint32_t)((i0 + u * stride) << 2);
+            const uint32_t c[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!((pk[u] >> (8 * q)) & 0xFFu)) {
+                    const unsigned long long key = ((unsigned long long)c[q] << 32) | (0xFFFFFFFFu - (v + q));
+                    best = key > best ? key : best;
+                }
             }
         }
     }
@@ -487,15 +507,37 @@ __device__ void team_cover(const SelectState& s, uint32_t j, Team t)
     if (nb) atomicAdd(&s.bmp_cov[j], nb);
 }
 
+// Shared memory of a selection block: the argmax reduction, the round's
+// update mode, and the picked vertex's ranges in every index segment.
+constexpr uint32_t kSegTab = 64;
+struct SelShared {
+    unsigned long long red[32];
+    uint64_t seg_a[kSegTab];    // first entry of the pick's list in segment g
+    uint64_t seg_end[kSegTab];  // end of segment g's part of the flattened lists
+    const uint32_t* seg_inv[kSegTab];
+    int mode;
+};
+
+// Set id at position f of the pick's flattened lists; g is the segment of
+// the caller's previous (smaller) position.
+__device__ __forceinline__ uint32_t flat_set(const SelShared* sh, uint64_t f, uint32_t& g)
+{
+    while (f >= sh->seg_end[g]) ++g;
+    const uint64_t first = g ? sh->seg_end[g - 1] : 0;
+    return sh->seg_inv[g][sh->seg_a[g] + (f - first)];
+}
+
 // Streams without bitmap-stored sets (small sets: decrementing is always the
 // cheaper update): cover and decrement in one pass, so a round needs one grid
-// barrier less; counts are identical to cover-then-decrement.  A segment of
-// the picked vertex's inverted list with few entries per warp of the team
-// goes one entry per warp (the set's members strided over the lanes), so the
-// round's covered sets spread over all warps; a long one goes 32 entries per
-// warp with the members of those sets flattened across the lanes.
+// barrier less; counts are identical to cover-then-decrement.  The picked
+// vertex's lists in all index segments are read as one flattened range,
+// their bounds loaded once per block, so no thread walks the segments one
+// after another.  A range with few entries per warp of the team goes one
+// entry per warp (the set's members strided over the lanes), so the round's
+// covered sets spread over all warps; a long one goes 32 entries per warp
+// with the members of those sets flattened across the lanes.
 template <class Team>
-__device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t)
+__device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, SelShared* sh)
 {
     const unsigned long long key = s.keys[j];
     const uint32_t v = 0xFFFFFFFFu - (uint32_t)key;
@@ -506,7 +548,85 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t)
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t gw = t.rank() >> 5, nw = t.size() >> 5;
     unsigned long long vol = 0, nnew = 0;
-    for (uint32_t g = 0; g < s.nsegs; ++g) {
+    if (s.nsegs <= kSegTab) {
+        if (threadIdx.x < 32) {
+            uint64_t a[2] = {0, 0}, len[2] = {0, 0};
+            const uint32_t* inv[2] = {nullptr, nullptr};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t g = lane + 32u * h;
+                if (g < s.nsegs) {
+                    const DevSegment sg = s.segs[g];
+                    a[h] = sg.voff[v];
+                    len[h] = sg.voff[v + 1] - a[h];
+                    inv[h] = sg.inv;
+                }
+            }
+            uint64_t run = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint64_t incl = len[h];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint64_t o = shfl64s_up(incl, d);
+                    if ((int)lane >= d) incl += o;
+                }
+                const uint32_t g = lane + 32u * h;
+                sh->seg_a[g] = a[h];
+                sh->seg_end[g] = run + incl;  // past nsegs: the total
+                sh->seg_inv[g] = inv[h];
+                run += shfl64s(incl, 31);
+            }
+        }
+        __syncthreads();
+        const uint64_t total = sh->seg_end[kSegTab - 1];
+        uint32_t g = 0;
+        if (total <= 4 * nw) {
+            for (uint64_t f = gw; f < total; f += nw) {
+                uint32_t take = 0;
+                uint64_t start = 0;
+                uint32_t len = 0;
+                if (lane == 0) {
+                    const uint32_t sid = flat_set(sh, f, g);
+                    if (!s.covered[sid]) {
+                        s.covered[sid] = 1;
+                        take = 1;
+                        start = s.off[sid];
+                        len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                    }
+                }
+                take = __shfl_sync(kFull, take, 0);
+                if (!take) continue;
+                start = shfl64s(start, 0);
+                len = __shfl_sync(kFull, len, 0);
+                for (uint32_t x = lane; x < len; x += 32) atomicAdd(&s.work[s.arena[start + x]], 0xFFFFFFFFu);
+                if (lane == 0) {
+                    vol += len;
+                    ++nnew;
+                }
+            }
+        } else {
+            for (uint64_t f0 = gw * 32; f0 < total; f0 += nw * 32) {
+                const uint64_t f = f0 + lane;
+                uint64_t start = 0;
+                uint32_t len = 0;
+                bool take = false;
+                if (f < total) {
+                    const uint32_t sid = flat_set(sh, f, g);
+                    if (!s.covered[sid]) {
+                        s.covered[sid] = 1;
+                        take = true;
+                        start = s.off[sid];
+                        len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                        vol += len;
+                        ++nnew;
+                    }
+                }
+                if (__any_sync(kFull, take)) warp_apply_sets(s.arena, start, len, s.work, 0xFFFFFFFFu);
+            }
+        }
+    }
+    for (uint32_t g = 0; s.nsegs > kSegTab && g < s.nsegs; ++g) {
         const uint64_t a = s.segs[g].voff[v], b = s.segs[g].voff[v + 1];
         const uint32_t* inv = s.segs[g].inv;
         if (b - a <= 4 * nw) {
@@ -710,12 +830,13 @@ __device__ void team_pick(const SelectState& s, uint32_t j, Team t, unsigned lon
 }
 
 template <class Team>
-__device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_mode, unsigned long long* s_red)
+__device__ void select_rounds(const SelectState& s, uint32_t k, Team t, SelShared* sh)
 {
+    int* s_mode = &sh->mode;
     for (uint32_t j = 0; j < k; ++j) {
-        team_pick(s, j, t, s_red);
+        team_pick(s, j, t, sh->red);
         if (s.nbmp == 0 && s.force_mode != 2) {
-            team_cover_decrement(s, j, t);
+            team_cover_decrement(s, j, t, sh);
             t.sync();
             continue;
         }
@@ -736,21 +857,23 @@ __device__ void select_rounds(const SelectState& s, uint32_t k, Team t, int* s_m
     }
 }
 
-__global__ void __launch_bounds__(512)
+// One 1024-thread CTA per SM: half the CTAs of two 512-thread ones, so each
+// grid barrier gathers half the arrivals.
+constexpr int kCoopThreads = 1024;
+
+__global__ void __launch_bounds__(kCoopThreads, 1)
 select_coop_kernel(SelectState s, uint32_t k)
 {
-    __shared__ int s_mode;
-    __shared__ unsigned long long s_red[32];
-    select_rounds(s, k, GridTeam{}, &s_mode, s_red);
+    __shared__ SelShared sh;
+    select_rounds(s, k, GridTeam{}, &sh);
 }
 
 __global__ void __launch_bounds__(512, 1)
 select_cta_kernel(const SelectState* states, const uint32_t* ks, uint32_t count)
 {
-    __shared__ int s_mode;
-    __shared__ unsigned long long s_red[32];
+    __shared__ SelShared sh;
     for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
-        select_rounds(states[i], ks[i], BlockTeam{}, &s_mode, s_red);
+        select_rounds(states[i], ks[i], BlockTeam{}, &sh);
         __syncthreads();
     }
 }
@@ -813,13 +936,12 @@ cudaError_t launch_prefix_count(const SelectState& s, uint64_t prefix, uint64_t 
 __global__ void __launch_bounds__(512, 1)
 select_cluster_kernel(const SelectState* states, const uint32_t* ks, uint32_t count)
 {
-    __shared__ int s_mode;
-    __shared__ unsigned long long s_red[32];
+    __shared__ SelShared sh;
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t nb = cl.num_blocks();
     const uint32_t cid = blockIdx.x / nb, ncl = gridDim.x / nb;
     for (uint32_t i = cid; i < count; i += ncl) {
-        select_rounds(states[i], ks[i], ClusterTeam{}, &s_mode, s_red);
+        select_rounds(states[i], ks[i], ClusterTeam{}, &sh);
         cl.sync();
     }
 }
@@ -852,15 +974,14 @@ cudaError_t launch_select_clusters(const SelectState* d_states, const uint32_t* 
 cudaError_t launch_select_all(const SelectState& s, uint32_t k, const DeviceInfo& di, cudaStream_t st)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_coop_kernel, 512, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_coop_kernel, kCoopThreads, 0);
     if (e != cudaSuccess) return e;
-    if (per_sm > 2) per_sm = 2;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    unsigned grid = (unsigned)(di.sms * per_sm);
+    unsigned grid = (unsigned)di.sms;
     SelectState sc = s;
     uint32_t kk = k;
     void* args[] = {&sc, &kk};
-    return cudaLaunchCooperativeKernel((void*)select_coop_kernel, dim3(grid), dim3(512), args, 0, st);
+    return cudaLaunchCooperativeKernel((void*)select_coop_kernel, dim3(grid), dim3(kCoopThreads), args, 0, st);
 }
 
 cudaError_t launch_select_batch(const SelectState* d_states, const uint32_t* d_ks, uint32_t count,

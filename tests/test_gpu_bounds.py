@@ -1,7 +1,7 @@
 """The bounds-checked build (-DIMM_BOUNDS_CHECK) on the paths the parity tests
 cover: IC on the weighted-cascade workload, fuzzed dense graphs, giant sets
-through both large-set paths (bitmap- and list-stored), LT walks including
-long ones, a small batch with both selection teams, and OPIM.  Every index
+through both large-set paths (bitmap- and list-stored), LT walks of every
+length (lane path, per-walk tables, bitmap slots), a small batch with both selection teams, and OPIM.  Every index
 check passes (a failed one returns an error) and every result equals the
 oracle's.  Each case runs in a process of its own that loads the checked
 library."""
@@ -71,6 +71,8 @@ n = 600
 row = np.arange(n + 1, dtype=np.uint64)
 src = np.array([(v + 1) % n for v in range(n)], dtype=np.uint32)
 stream_equal(graphgen.Graph(n=n, row=row, src=src, weight=np.ones(n, dtype=np.float32), model=graphgen.LT), 50, 2, (3,))
+from test_gpu_parity import chain_graph
+stream_equal(chain_graph([900, 1500, 1800] * 10), 3000, 8, (1, 20))
 """,
     "batch_opim": """
 b = graphgen.batch_workload(count=8, max_log_n=15.0)

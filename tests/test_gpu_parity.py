@@ -160,6 +160,39 @@ def test_lt_long_walks(imm):
     check_stream(imm, ctx, cyc, 300, 3)
 
 
+def chain_graph(lengths, w_back1=0.7, w_back2=0.3):
+    """Disjoint chains; position p of a chain has in-edges from p - 1
+    (w_back1) and p - 2 (w_back2), so a reverse walk from p runs back to the
+    chain's start with a random length of about p / 1.3 steps."""
+    edges, w = [], []
+    base = 0
+    for L in lengths:
+        for p in range(1, L):
+            edges.append((base + p - 1, base + p))
+            w.append(w_back1 if p > 1 else 1.0)
+            if p > 1:
+                edges.append((base + p - 2, base + p))
+                w.append(w_back2)
+        base += L
+    return edges_to_graph(base, edges, w, LT)
+
+
+def test_lt_walks_of_every_length(imm):
+    # n = 42,000 (bitmaps of 1,313 words): walks up to 160 steps on the lane
+    # path, up to 1,024 with per-walk tables, longer ones on the bitmap slots
+    # (lists up to 1,313 members, bitmaps beyond)
+    g = chain_graph([900, 1500, 1800] * 10)
+    ctx = new_ctx(imm, g)
+    o = check_stream(imm, ctx, g, 3000, 8)
+    off, _ = imm.imm_get_sets(ctx, 0, 3000, members=False)
+    lens = np.diff(off.astype(np.int64))
+    assert (lens > 1024).any() and ((lens > 160) & (lens <= 1024)).sum() > 1000 and (lens > 1313).any()
+    for k in (1, 20):
+        s1, c1 = imm.imm_select(ctx, k)
+        s2, c2 = o.select(k)
+        assert np.array_equal(s1, s2) and c1 == c2
+
+
 def test_stream_extension_is_prefix_stable(imm, large_path):
     g = graphgen.make_graph(2048, 16384, 21, IC, "uniform", pmax=0.2)
     a = new_ctx(imm, g)
