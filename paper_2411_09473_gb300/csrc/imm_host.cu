@@ -1347,13 +1347,14 @@ int job_after_select(Job& j, uint64_t cov)
         if (nF >= (1.0 + j.plan.eps_p) * x) {
             j.lb = nF / (1.0 + j.plan.eps_p);
             j.st.stopped_early = 1;
-            return job_final_target(j);
-        }
-        if (j.i < j.plan.rounds) {
+        } else if (j.i < j.plan.rounds) {
             ++j.i;
             return job_round_target(j);
         }
-        return job_final_target(j);
+        TRY(job_final_target(j));
+        // theta within this round's sets: the final selection sees exactly
+        // this round's sets, so this round's seeds and coverage are final
+        if (j.target != j.round_sets) return IMM_OK;
     }
     // final selection
     std::memcpy(j.seeds_out, w->pin_seeds, (size_t)j.k * 4);
@@ -1745,6 +1746,7 @@ int imm_run_ex(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, ui
     st.lambda_star = lam_s;
 
     double lb = 1.0;
+    uint64_t last_cov = 0, last_sets = 0;  // the last round's selection
     for (uint32_t i = 1; i <= rounds; i++) {
         const double x = std::ldexp(nd, -(int)i);
         const double th = std::ceil(lam_p / x);
@@ -1753,6 +1755,8 @@ int imm_run_ex(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, ui
         TRY(sample_to(c, theta_i, rng_seed));
         uint64_t cov = 0;
         TRY(select_k(c, k, seeds_out, &cov));
+        last_cov = cov;
+        last_sets = c->nsets;
         const double nF = nd * (double)cov / (double)c->nsets;
         if (i - 1 < IMM_MAX_ROUNDS) {
             st.theta_i[i - 1] = theta_i;
@@ -1771,14 +1775,19 @@ int imm_run_ex(imm_ctx* c, int model, uint32_t k, double epsilon, double ell, ui
     const uint64_t theta = (uint64_t)tf;
     st.lb = lb;
     st.theta = theta;
+    bool reuse = false;
     if (flags & IMM_RUN_FRESH_FINAL) {
         drop_stream(c);
         TRY(sample_to(c, theta, rng_seed ^ IMM_FRESH_FINAL_KEY));
     } else {
         TRY(sample_to(c, std::max<uint64_t>(theta, c->nsets), rng_seed));
+        // theta within the stream the last round selected over: the final
+        // selection's sets are that round's, so its seeds (already in
+        // seeds_out) and coverage are the final ones
+        reuse = last_sets > 0 && c->nsets == last_sets;
     }
-    uint64_t cov = 0;
-    TRY(select_k(c, k, seeds_out, &cov));
+    uint64_t cov = last_cov;
+    if (!reuse) TRY(select_k(c, k, seeds_out, &cov));
     st.num_sets = c->nsets;
     st.covered = cov;
     st.members = c->nmembers;

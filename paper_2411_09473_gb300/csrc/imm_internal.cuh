@@ -183,6 +183,14 @@ constexpr bool kBoundsChecked = true;
 #define IMM_IN_BOUNDS(idx, bound, err, where) true
 constexpr bool kBoundsChecked = false;
 #endif
+// LT guide entries (one per in-edge): heads of at most kGuideRelMax in-edges
+// store the candidate edge relative to their first in-edge in 16 bits and
+// the tail's in-degree in 23 (kGuideDegRel: unknown, read the row); larger
+// heads store it absolutely and the degree in 7 bits (kGuideDegAbs)
+constexpr uint32_t kGuideRelMax = 0xFFFFu;
+constexpr uint32_t kGuideDegRel = (1u << 23) - 1u;
+constexpr uint32_t kGuideDegAbs = 127u;
+
 // where codes of the checks
 enum : uint32_t {
     kChkStage = 1, kChkLargeQ, kChkSlotQueue, kChkSlotBitmap, kChkBig, kChkArena, kChkInv, kChkGroupSmall,

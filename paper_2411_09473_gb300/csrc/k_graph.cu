@@ -87,9 +87,11 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
 // head v of in-degree d, bucket b < d covers the 24-bit draws r with
 // floor(r * d / 2^24) = b, whose smallest is lo_b = ceil(b * 2^24 / d).  The
 // entry of bucket b is (j, cthr[j], src[j], 0) for j = the first in-edge of v
-// with cthr[j] > lo_b, packed as (j, cthr[j] | min(deg(u), 127) << 25, u,
-// row[u]) with u = src[j]: the tail u and, when its in-degree is below 127,
-// u's in-edge range, which the walk's next step needs.  A draw r in bucket b
+// with cthr[j] > lo_b, packed with u = src[j] as (j, cthr[j] | deg(u) << 25,
+// u, row[u]): the tail u and u's in-edge range, which the walk's next step
+// needs.  deg(u) takes the 7 bits above cthr and, for heads of fewer than
+// 2^16 in-edges (j stored relative to row[v] in the low 16 bits of x), the 16
+// high bits of x as well; its top value stands for "read u's row".  A draw r in bucket b
 // has its answer (the first j with r < cthr[j]) at that j whenever r <
 // cthr[j], which the entry tells with the next vertex in hand; otherwise the
 // scan continues over cthr from j + 1.  The same answer as a search over all
@@ -105,11 +107,18 @@ __global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, const
         for (uint64_t b = 0; b < d; ++b) {
             const uint64_t lo = ((b << 24) + d - 1) / d;
             while (j < re && (uint64_t)cthr[j] <= lo) ++j;
-            uint4 e = make_uint4(re, 0u, 0u, 0u);
+            // heads with fewer than 2^16 in-edges keep j relative to their
+            // first in-edge in 16 bits, which leaves 16 more bits for the
+            // tail's in-degree (23 in all; the top value means "read the row")
+            const bool rel = d <= kGuideRelMax;
+            uint4 e = make_uint4(rel ? re - rs : re, 0u, 0u, 0u);
             if (j < re) {
                 const uint32_t u = src[j];
                 const uint64_t du = row[u + 1] - row[u];
-                e = make_uint4(j, cthr[j] | ((uint32_t)(du < 127 ? du : 127) << 25), u, (uint32_t)row[u]);
+                const uint32_t dmax = rel ? kGuideDegRel : kGuideDegAbs;
+                const uint32_t dc = du < dmax ? (uint32_t)du : dmax;
+                const uint32_t x = rel ? (j - rs) | ((dc >> 7) << 16) : j;
+                e = make_uint4(x, cthr[j] | ((dc & 127u) << 25), u, (uint32_t)row[u]);
             }
             guide[rs + b] = e;
         }

@@ -628,13 +628,14 @@ cudaError_t launch_ic_large(const DevGraph& g, const SampleBatch& b, const Large
 // ===========================================================================
 // LT, small path: one lane per walk, path kept in shared memory.
 // ===========================================================================
-constexpr int kLtThreads = 64;  // path[kLtCap][kLtThreads] stays within static shared memory
+constexpr int kLtThreads = 64;  // path and filter stay within static shared memory
 
 // One step of the reverse walk at a vertex with in-edge range [lo, hi): the
 // first j in [lo, hi) with r < cthr[j] (cthr is nondecreasing), or hi; the
 // tail u of j and u's in-edge range [*ulo, *uhi).  The guide entry of r's
 // bucket is the answer when r is below its threshold, and it carries u and
-// (in-degree below 127) u's range; otherwise a short scan and row reads.
+// (unless u's in-degree is too large for its field) u's range; otherwise a
+// short scan and row reads.
 constexpr uint32_t kCthrMask = (1u << 25) - 1;
 
 // The guide entry a walk step at a vertex with in-edges [lo, hi) and draw r
@@ -652,11 +653,12 @@ __device__ __forceinline__ uint32_t lt_resolve(const DevGraph& g, uint32_t lo, u
                                                uint32_t* u, uint32_t* ulo, uint32_t* uhi)
 {
     if (hi == lo) return hi;
-    uint32_t j = e.x;
+    const bool rel = hi - lo <= kGuideRelMax;
+    uint32_t j = rel ? lo + (e.x & 0xFFFFu) : e.x;
     if (j < hi && r < (e.y & kCthrMask)) {
         *u = e.z;
-        const uint32_t du = e.y >> 25;
-        if (du < 127) {
+        const uint32_t du = rel ? (e.y >> 25) | ((e.x >> 16) << 7) : e.y >> 25;
+        if (du < (rel ? kGuideDegRel : kGuideDegAbs)) {
             *ulo = e.w;
             *uhi = e.w + du;
         } else {

@@ -514,7 +514,8 @@ struct SelShared {
     unsigned long long red[32];
     uint64_t seg_a[kSegTab];    // first entry of the pick's list in segment g
     uint64_t seg_end[kSegTab];  // end of segment g's part of the flattened lists
-    const uint32_t* seg_inv[kSegTab];
+    const uint32_t* seg_inv[kSegTab];   // the segments, loaded once per selection
+    const uint64_t* seg_voff[kSegTab];
     int mode;
 };
 
@@ -551,15 +552,13 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, S
     if (s.nsegs <= kSegTab) {
         if (threadIdx.x < 32) {
             uint64_t a[2] = {0, 0}, len[2] = {0, 0};
-            const uint32_t* inv[2] = {nullptr, nullptr};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t g = lane + 32u * h;
                 if (g < s.nsegs) {
-                    const DevSegment sg = s.segs[g];
-                    a[h] = sg.voff[v];
-                    len[h] = sg.voff[v + 1] - a[h];
-                    inv[h] = sg.inv;
+                    const uint64_t* voff = sh->seg_voff[g];
+                    a[h] = voff[v];
+                    len[h] = voff[v + 1] - a[h];
                 }
             }
             uint64_t run = 0;
@@ -574,7 +573,6 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, S
                 const uint32_t g = lane + 32u * h;
                 sh->seg_a[g] = a[h];
                 sh->seg_end[g] = run + incl;  // past nsegs: the total
-                sh->seg_inv[g] = inv[h];
                 run += shfl64s(incl, 31);
             }
         }
@@ -587,12 +585,15 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, S
                 uint64_t start = 0;
                 uint32_t len = 0;
                 if (lane == 0) {
+                    // the set's covered flag and extent are read together
                     const uint32_t sid = flat_set(sh, f, g);
-                    if (!s.covered[sid]) {
+                    const uint8_t cv = s.covered[sid];
+                    const uint64_t o0 = __ldg(s.off + sid), o1 = __ldg(s.off + (uint64_t)sid + 1);
+                    if (!cv) {
                         s.covered[sid] = 1;
                         take = 1;
-                        start = s.off[sid];
-                        len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                        start = o0;
+                        len = (uint32_t)(o1 - o0);
                     }
                 }
                 take = __shfl_sync(kFull, take, 0);
@@ -613,11 +614,13 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, S
                 bool take = false;
                 if (f < total) {
                     const uint32_t sid = flat_set(sh, f, g);
-                    if (!s.covered[sid]) {
+                    const uint8_t cv = s.covered[sid];
+                    const uint64_t o0 = __ldg(s.off + sid), o1 = __ldg(s.off + (uint64_t)sid + 1);
+                    if (!cv) {
                         s.covered[sid] = 1;
                         take = true;
-                        start = s.off[sid];
-                        len = (uint32_t)(s.off[(uint64_t)sid + 1] - start);
+                        start = o0;
+                        len = (uint32_t)(o1 - o0);
                         vol += len;
                         ++nnew;
                     }
@@ -833,6 +836,12 @@ template <class Team>
 __device__ void select_rounds(const SelectState& s, uint32_t k, Team t, SelShared* sh)
 {
     int* s_mode = &sh->mode;
+    if (s.nsegs <= kSegTab && threadIdx.x < s.nsegs) {
+        const DevSegment sg = s.segs[threadIdx.x];
+        sh->seg_voff[threadIdx.x] = sg.voff;
+        sh->seg_inv[threadIdx.x] = sg.inv;
+    }
+    __syncthreads();
     for (uint32_t j = 0; j < k; ++j) {
         team_pick(s, j, t, sh->red);
         if (s.nbmp == 0 && s.force_mode != 2) {
