@@ -320,12 +320,15 @@ struct ClusterTeam {
 template <class Team>
 __device__ void team_argmax(const SelectState& s, uint32_t j, Team t, unsigned long long* s_red)
 {
-    // four vertices per load with 16-byte count loads (work is 256-byte
+    // Four vertices per load with 16-byte count loads (work is 256-byte
     // aligned), eight loads issued before any is used (the counts sit in L2:
-    // the pass is bound by load latency, not bandwidth); the ragged tail one
-    // by one
+    // the pass is bound by load latency and issue, not bandwidth).  A thread
+    // meets its vertices in increasing order, so among equal counts the
+    // first one it meets is the lowest id and a strict comparison keeps it:
+    // (count, vertex) is packed into the round's key once per thread, not
+    // per vertex.  bc holds count + 1 (0: no unpicked vertex met yet).
     constexpr int kU = 8;
-    unsigned long long best = 0;
+    uint32_t bc = 0, bv = 0;
     const uint64_t n4 = s.n >> 2;
     const uint4* w4 = reinterpret_cast<const uint4*>(s.work);
     const uint32_t* p4 = reinterpret_cast<const uint32_t*>(s.picked);
@@ -343,21 +346,35 @@ __device__ void team_argmax(const SelectState& s, uint32_t j, Team t, unsigned l
         for (int u = 0; u < kU; ++u) {
             const uint32_t v = (uint32_t)((i0 + u * stride) << 2);
             const uint32_t c[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+            if (pk[u] == 0u) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!((pk[u] >> (8 * q)) & 0xFFu)) {
-                    const unsigned long long key = ((unsigned long long)c[q] << 32) | (0xFFFFFFFFu - (v + q));
-                    best = key > best ? key : best;
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t cq = c[q] + 1u;
+                    if (cq > bc) {
+                        bc = cq;
+                        bv = v + q;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t cq = c[q] + 1u;
+                    if (!((pk[u] >> (8 * q)) & 0xFFu) && cq > bc) {
+                        bc = cq;
+                        bv = v + q;
+                    }
                 }
             }
         }
     }
     for (uint64_t v = (n4 << 2) + t.rank(); v < s.n; v += t.size()) {
-        if (!s.picked[v]) {
-            const unsigned long long key = ((unsigned long long)s.work[v] << 32) | (0xFFFFFFFFu - (uint32_t)v);
-            best = key > best ? key : best;
+        const uint32_t cq = s.work[v] + 1u;
+        if (!s.picked[v] && cq > bc) {
+            bc = cq;
+            bv = (uint32_t)v;
         }
     }
+    unsigned long long best = bc ? ((unsigned long long)(bc - 1u) << 32) | (0xFFFFFFFFu - bv) : 0ull;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         const unsigned long long o = __shfl_xor_sync(kFull, best, d);
