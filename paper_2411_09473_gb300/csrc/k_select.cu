@@ -49,13 +49,35 @@ __device__ __forceinline__ uint32_t owner_lane(uint32_t j, uint32_t incl)
     return o;
 }
 
+// atomicAdd(&work[u], delta) for every member u of one set (arena[start ..
+// start + len)), strided over the lanes of the calling warp with eight member
+// loads in flight per lane: a set of a few hundred members costs one or two
+// load round trips, not one per 32 members.
+constexpr uint32_t kNoMember = 0xFFFFFFFFu;  // never a vertex id (n < 2^32)
+__device__ __forceinline__ void warp_apply_one(const uint32_t* arena, uint64_t start, uint32_t len, uint32_t* work,
+                                               uint32_t delta, uint32_t lane)
+{
+    for (uint32_t x0 = lane; x0 < len; x0 += 32u * 8u) {
+        uint32_t m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t x = x0 + 32u * u;
+            m[u] = x < len ? __ldg(arena + start + x) : kNoMember;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (m[u] != kNoMember) atomicAdd(&work[m[u]], delta);
+    }
+}
+
 // Every member u of the sets given by (start, len) per lane gets
 // atomicAdd(&work[u], delta).  Warp-cooperative: sets of >= 32 members one at
-// a time across the warp, shorter ones flattened across lanes.
+// a time across the warp, shorter ones flattened across lanes (four member
+// loads in flight per lane).
 __device__ __forceinline__ void warp_apply_sets(const uint32_t* arena, uint64_t start, uint32_t len, uint32_t* work,
                                                 uint32_t delta)
 {
-    const int lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31;
     const bool big = len >= 32;
     uint32_t bigmask = __ballot_sync(kFull, big);
     while (bigmask) {
@@ -63,23 +85,30 @@ __device__ __forceinline__ void warp_apply_sets(const uint32_t* arena, uint64_t 
         bigmask &= bigmask - 1;
         const uint32_t L = __shfl_sync(kFull, len, o);
         const uint64_t A = shfl64s(start, o);
-        for (uint32_t i = lane; i < L; i += 32) atomicAdd(&work[arena[A + i]], delta);
+        warp_apply_one(arena, A, L, work, delta, lane);
     }
     const uint32_t sl = big ? 0u : len;
     uint32_t incl = sl;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint32_t t = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += t;
+        if ((int)lane >= d) incl += t;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     const uint32_t excl = incl - sl;
-    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        const uint32_t o = owner_lane(j, incl);
-        const uint64_t A = shfl64s(start, o);
-        const uint32_t ex = __shfl_sync(kFull, excl, o);
-        if (j < total) atomicAdd(&work[arena[A + (j - ex)]], delta);
+    for (uint32_t j0 = 0; j0 < total; j0 += 32u * 4u) {
+        uint32_t m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + 32u * u + lane;
+            const uint32_t o = owner_lane(j, incl);
+            const uint64_t A = shfl64s(start, o);
+            const uint32_t ex = __shfl_sync(kFull, excl, o);
+            m[u] = j < total ? __ldg(arena + A + (j - ex)) : kNoMember;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (m[u] != kNoMember) atomicAdd(&work[m[u]], delta);
     }
 }
 
@@ -617,7 +646,7 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, S
                 if (!take) continue;
                 start = shfl64s(start, 0);
                 len = __shfl_sync(kFull, len, 0);
-                for (uint32_t x = lane; x < len; x += 32) atomicAdd(&s.work[s.arena[start + x]], 0xFFFFFFFFu);
+                warp_apply_one(s.arena, start, len, s.work, 0xFFFFFFFFu, lane);
                 if (lane == 0) {
                     vol += len;
                     ++nnew;
@@ -667,7 +696,7 @@ __device__ void team_cover_decrement(const SelectState& s, uint32_t j, Team t, S
                 if (!take) continue;
                 start = shfl64s(start, 0);
                 len = __shfl_sync(kFull, len, 0);
-                for (uint32_t x = lane; x < len; x += 32) atomicAdd(&s.work[s.arena[start + x]], 0xFFFFFFFFu);
+                warp_apply_one(s.arena, start, len, s.work, 0xFFFFFFFFu, lane);
                 if (lane == 0) {
                     vol += len;
                     ++nnew;
