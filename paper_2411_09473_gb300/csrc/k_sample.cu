@@ -686,6 +686,36 @@ __device__ __forceinline__ uint32_t lt_resolve(const DevGraph& g, uint32_t lo, u
 constexpr int kLtFiltWords = 32;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
+// One thread's copy of src[0, len) to dst + pos (dst's bound cap) and
+// clearing of tab[slots[0, len)], eight loads in flight at a time: a walk of
+// hundreds of members costs tens of round trips, not hundreds.
+__device__ __forceinline__ void thread_copy(uint32_t* dst, uint64_t pos, uint64_t cap, const uint32_t* src,
+                                            uint32_t len, unsigned long long* err, uint32_t where)
+{
+    for (uint32_t i0 = 0; i0 < len; i0 += 8) {
+        uint32_t t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = i0 + u < len ? src[i0 + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + u < len && IMM_IN_BOUNDS(pos + i0 + u, cap, err, where)) dst[pos + i0 + u] = t[u];
+    }
+    (void)err;
+    (void)where;
+}
+
+__device__ __forceinline__ void thread_clear(uint32_t* tab, const uint32_t* slots, uint32_t len)
+{
+    for (uint32_t i0 = 0; i0 < len; i0 += 8) {
+        uint32_t t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = i0 + u < len ? slots[i0 + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + u < len) tab[t[u]] = 0u;
+    }
+}
+
 __device__ __forceinline__ uint32_t lt_mid_hash(uint32_t u)
 {
     return (u * 0x9E3779B1u) >> (32 - kLtMidHashBits);
@@ -829,15 +859,15 @@ lt_small_kernel(DevGraph g, SampleBatch b, MidSlots ms)
                 const uint32_t pl = len < kLtCap ? len : kLtCap;
                 for (uint32_t i = 0; i < pl; ++i)
                     if (IMM_IN_BOUNDS(pos + i, b.stage_cap, b.sc->bounds, kChkStage)) b.stage[pos + i] = path[i][tid];
-                for (uint32_t i = pl; i < len; ++i)
-                    if (IMM_IN_BOUNDS(pos + i, b.stage_cap, b.sc->bounds, kChkStage))
-                        b.stage[pos + i] = ms.path[(uint64_t)slot * kLtMidCap + (i - kLtCap)];
+                if (len > pl)
+                    thread_copy(b.stage, pos + pl, b.stage_cap, ms.path + (uint64_t)slot * kLtMidCap, len - pl,
+                                b.sc->bounds, kChkStage);
             }
         }
         // the walk ends here (stored, or handed on): clear its table entries
         // and its filter
         if (slot != kNoSlot) {
-            for (uint32_t i = kLtCap; i < len; ++i) tab[ms.hpos[(uint64_t)slot * kLtMidCap + (i - kLtCap)]] = 0u;
+            if (len > kLtCap) thread_clear(tab, ms.hpos + (uint64_t)slot * kLtMidCap, len - kLtCap);
             slot = kNoSlot;
         }
 #pragma unroll
@@ -923,7 +953,7 @@ lt_mid_kernel(DevGraph g, SampleBatch b, MidSlots ms)
             r = r2;
             e = e2;
         }
-        for (uint32_t i = 0; i < len; ++i) tab[hpos[i]] = 0u;
+        thread_clear(tab, hpos, len);
         if (over) {
             const uint32_t o = atomicAdd(&b.sc->long_count, 1u);
             if (IMM_IN_BOUNDS(o, b.count, b.sc->bounds, kChkLongQ)) b.long_q[o] = rel;
@@ -932,9 +962,7 @@ lt_mid_kernel(DevGraph g, SampleBatch b, MidSlots ms)
         b.set_edges[rel] = len;
         uint64_t pos = 0;
         if (reserve_big(b, rel, len, 0u, &pos)) {
-            uint32_t* out = b.big + pos;
-            for (uint32_t i = 0; i < len; ++i)
-                if (IMM_IN_BOUNDS(pos + i, b.big_cap, b.sc->bounds, kChkBig)) out[i] = path[i];
+            thread_copy(b.big, pos, b.big_cap, path, len, b.sc->bounds, kChkBig);
         }
     }
 }
