@@ -57,6 +57,10 @@ ALU_OPS_PER_QUAD_EVAL = 44
 # DRAM bytes per quad evaluation of the dominant IC kernel on the 1M-vertex
 # workload, from one ncu capture (profiles/ic_group_kernel__ic_u01_1m_first20000sets.md)
 IC_DRAM_BYTES_PER_QUAD_EVAL = 32.628760e9 / 12215037853
+# DRAM bytes per member of the LT walk sampler on the 4M-vertex LT workload,
+# from one ncu capture of a 46,669-set call with 2,105,421 members
+# (profiles/lt_samplers_and_select_coop__lt_4m_46669sets_k100.md)
+LT_DRAM_BYTES_PER_MEMBER = (329.627904e6 + 7.699712e6) / 2105421
 WORKLOADS = ("ic_u01_1m", "lt_4m", "ic_wc_4k", "ic_u1_256k", "batch64", "served")
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
@@ -456,7 +460,10 @@ def run_plain(args, dist: Dist, name: str, steps: int, warmup: int, e2e_on: bool
         peak, peak_kind = measured_peaks()
         roof = {"kernel": "RRR sampling (LT): lt_small_kernel + lt_mid_kernel + lt_long_kernel", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": peak_kind, "traffic": None,
+                "peak_kind": peak_kind,
+                "traffic": (LT_DRAM_BYTES_PER_MEMBER * members / max(launches, 1) if name == "lt_4m" else None),
+                "traffic_source": "ncu dram__bytes_read+write per member of lt_small_kernel, scaled to the "
+                                  "average timed launch",
                 "algorithmic_bytes": "8 B per walk step + 16 B per member",
                 "algorithmic_bytes_per_launch": algo_bytes / max(launches, 1), "launches": launches}
     gteps = (st.sample_edges / (st.ms_sample / 1e3)) / 1e9 if st.ms_sample > 0 else 0.0
