@@ -96,31 +96,49 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
 // cthr[j], which the entry tells with the next vertex in hand; otherwise the
 // scan continues over cthr from j + 1.  The same answer as a search over all
 // of v's in-edges, usually in one read.
-__global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, const uint32_t* src, uint32_t n,
-                                uint4* guide)
+// Number of buckets b of a head of in-degree d whose smallest draw
+// lo_b = ceil(b * 2^24 / d) is below t: floor((t - 1) d / 2^24) + 1 (0 for
+// t = 0).  In-edge j is the entry of exactly the buckets with
+// cthr[j-1] <= lo_b < cthr[j], i.e. b in [nb(cthr[j-1]), nb(cthr[j])) (the
+// first in-edge from 0); buckets from nb(cthr[last]) on have no in-edge.
+__device__ __forceinline__ uint64_t guide_nb(uint32_t t, uint64_t d)
 {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    return t == 0u ? 0ull : (((uint64_t)(t - 1u) * d) >> 24) + 1ull;
+}
+
+// One warp per head, its lanes over the in-edges: each in-edge writes the
+// buckets it answers (one on average), so a head of 10^5 in-edges is not one
+// thread's serial loop.
+__global__ void __launch_bounds__(256)
+lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, const uint32_t* src, uint32_t n, uint4* guide)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = gw; v < n; v += nw) {
         const uint32_t rs = (uint32_t)row[v], re = (uint32_t)row[v + 1];
         const uint64_t d = re - rs;
-        uint32_t j = rs;
-        for (uint64_t b = 0; b < d; ++b) {
-            const uint64_t lo = ((b << 24) + d - 1) / d;
-            while (j < re && (uint64_t)cthr[j] <= lo) ++j;
-            // heads with fewer than 2^16 in-edges keep j relative to their
-            // first in-edge in 16 bits, which leaves 16 more bits for the
-            // tail's in-degree (23 in all; the top value means "read the row")
-            const bool rel = d <= kGuideRelMax;
-            uint4 e = make_uint4(rel ? re - rs : re, 0u, 0u, 0u);
-            if (j < re) {
+        // heads with fewer than 2^16 in-edges keep j relative to their
+        // first in-edge in 16 bits, which leaves 16 more bits for the
+        // tail's in-degree (23 in all; the top value means "read the row")
+        const bool rel = d <= kGuideRelMax;
+        for (uint32_t j = rs + lane; j < re; j += 32) {
+            const uint32_t tj = cthr[j];
+            const uint64_t b0 = guide_nb(j > rs ? cthr[j - 1] : 0u, d);
+            const uint64_t b1 = guide_nb(tj, d) < d ? guide_nb(tj, d) : d;
+            if (b0 < b1) {
                 const uint32_t u = src[j];
                 const uint64_t du = row[u + 1] - row[u];
                 const uint32_t dmax = rel ? kGuideDegRel : kGuideDegAbs;
                 const uint32_t dc = du < dmax ? (uint32_t)du : dmax;
                 const uint32_t x = rel ? (j - rs) | ((dc >> 7) << 16) : j;
-                e = make_uint4(x, cthr[j] | ((dc & 127u) << 25), u, (uint32_t)row[u]);
+                const uint4 e = make_uint4(x, tj | ((dc & 127u) << 25), u, (uint32_t)row[u]);
+                for (uint64_t b = b0; b < b1; ++b) guide[rs + b] = e;
             }
-            guide[rs + b] = e;
+            if (j == re - 1u) {
+                const uint4 none = make_uint4(rel ? re - rs : re, 0u, 0u, 0u);
+                for (uint64_t b = b1; b < d; ++b) guide[rs + b] = none;
+            }
         }
     }
 }
@@ -128,7 +146,10 @@ __global__ void lt_guide_kernel(const uint64_t* row, const uint32_t* cthr, const
 cudaError_t launch_lt_guide(const uint64_t* row, const uint32_t* cthr, const uint32_t* src, uint32_t n,
                             uint4* guide, cudaStream_t st)
 {
-    lt_guide_kernel<<<(n + 255) / 256, 256, 0, st>>>(row, cthr, src, n, guide);
+    uint64_t blocks = ((uint64_t)n + 7) / 8;  // 8 warps (heads) per block
+    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+    if (blocks == 0) blocks = 1;
+    lt_guide_kernel<<<(unsigned)blocks, 256, 0, st>>>(row, cthr, src, n, guide);
     return cudaGetLastError();
 }
 
