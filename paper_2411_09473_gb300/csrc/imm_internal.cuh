@@ -132,10 +132,11 @@ struct DevGraph {
     const uint64_t* row;  // n+1 in-edge offsets (CSR of G^T)
     const uint32_t* src;  // m (padded to a multiple of 4): tail of each in-edge
     const uint32_t* thr;  // m (padded, zeros): IC threshold or LT cumulative threshold
-    const uint4* guide;     // LT only, m: guide[row[v] + b] = (j, cthr[j] | min(indeg(u), 127) << 25,
+    const uint4* guide;     // LT only, m: guide[row[v] + b] = (j, cthr[j] | indeg(u) << 25,
                             // u = src[j], row[u]) for j the first in-edge of v with
                             // cthr[j] > ceil(b * 2^24 / indeg(v)), b < indeg(v)
-                            // ((row[v+1], 0, 0, 0) when there is none)
+                            // (no such j: j = row[v+1], the rest 0); j and indeg(u)
+                            // packed as kGuideRelMax / kGuideDegRel / kGuideDegAbs say
 };
 
 // Counters and flags of one sampling batch (device memory, zeroed per batch

@@ -56,19 +56,56 @@ __global__ void ic_threshold_kernel(const float* w, uint64_t m, uint32_t* thr)
     }
 }
 
-// One thread per head: the running sum is sequential by definition.
-__global__ void lt_threshold_kernel(const uint64_t* row, const float* w, uint32_t n, uint32_t* cthr, int* flags)
+// One warp per head.  The running sum is sequential by definition, but when
+// every weight of the head is 0 or at least 2^-29 (so a multiple of 2^-52)
+// and the head's sum is below 2, every partial sum is a multiple of 2^-52
+// below 2, which fp64 holds exactly: no addition rounds, and a warp scan in
+// any order gives the sequential sums bit for bit.  Other heads take the
+// sequential loop on one lane.
+__global__ void __launch_bounds__(256)
+lt_threshold_kernel(const uint64_t* row, const float* w, uint32_t n, uint32_t* cthr, int* flags)
 {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        double cw = 0.0;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = gw; v < n; v += nw) {
         const uint64_t lo = row[v], hi = row[v + 1];
-        for (uint64_t e = lo; e < hi; ++e) {
-            cw = __dadd_rn(cw, (double)w[e]);
-            const double t = ceil(__dmul_rn(cw, 16777216.0));
-            cthr[e] = t > 16777216.0 ? kQ24 : (uint32_t)t;
+        bool ok = true;
+        double part = 0.0;
+        for (uint64_t e = lo + lane; e < hi; e += 32) {
+            const float x = w[e];
+            ok = ok && (x == 0.0f || (x >= 0x1p-29f && x <= 1.0f));
+            part = __dadd_rn(part, (double)x);
         }
-        if (cw > 1.0 + 1e-6) atomicOr(flags, kFlagLtSum);
+        ok = __all_sync(kFull, ok);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) part = __dadd_rn(part, __shfl_xor_sync(kFull, part, d));
+        if (ok && part < 2.0) {
+            double carry = 0.0;
+            for (uint64_t e0 = lo; e0 < hi; e0 += 32) {
+                const uint64_t e = e0 + lane;
+                double x = e < hi ? (double)w[e] : 0.0;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const double y = __shfl_up_sync(kFull, x, d);
+                    if ((int)lane >= d) x = __dadd_rn(x, y);
+                }
+                if (e < hi) {
+                    const double t = ceil(__dmul_rn(__dadd_rn(carry, x), 16777216.0));
+                    cthr[e] = t > 16777216.0 ? kQ24 : (uint32_t)t;
+                }
+                carry = __dadd_rn(carry, __shfl_sync(kFull, x, 31));
+            }
+            if (lane == 0 && part > 1.0 + 1e-6) atomicOr(flags, kFlagLtSum);
+        } else if (lane == 0) {
+            double cw = 0.0;
+            for (uint64_t e = lo; e < hi; ++e) {
+                cw = __dadd_rn(cw, (double)w[e]);
+                const double t = ceil(__dmul_rn(cw, 16777216.0));
+                cthr[e] = t > 16777216.0 ? kQ24 : (uint32_t)t;
+            }
+            if (cw > 1.0 + 1e-6) atomicOr(flags, kFlagLtSum);
+        }
     }
 }
 
@@ -78,7 +115,10 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
     if (model == 0) {
         if (m) ic_threshold_kernel<<<2048, 256, 0, st>>>(w, m, thr);
     } else {
-        lt_threshold_kernel<<<(n + 255) / 256, 256, 0, st>>>(row, w, n, thr, d_flags);
+        uint64_t blocks = ((uint64_t)n + 7) / 8;  // 8 warps (heads) per block
+        if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+        if (blocks == 0) blocks = 1;
+        lt_threshold_kernel<<<(unsigned)blocks, 256, 0, st>>>(row, w, n, thr, d_flags);
     }
     return cudaGetLastError();
 }
@@ -96,6 +136,7 @@ cudaError_t launch_thresholds(const uint64_t* row, const float* w, uint32_t n, u
 // cthr[j], which the entry tells with the next vertex in hand; otherwise the
 // scan continues over cthr from j + 1.  The same answer as a search over all
 // of v's in-edges, usually in one read.
+
 // Number of buckets b of a head of in-degree d whose smallest draw
 // lo_b = ceil(b * 2^24 / d) is below t: floor((t - 1) d / 2^24) + 1 (0 for
 // t = 0).  In-edge j is the entry of exactly the buckets with
