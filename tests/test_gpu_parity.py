@@ -193,6 +193,39 @@ def test_lt_walks_of_every_length(imm):
         assert np.array_equal(s1, s2) and c1 == c2
 
 
+def test_lt_guide_layouts_and_misses(imm):
+    """Heads of 65,535 and 70,000 in-edges (the two guide entry layouts, j
+    relative or absolute), uneven weights with "none" mass (guide misses and
+    threshold scans), and tails of in-degree 2..300 (degrees inside and past
+    the 7-bit field of the absolute layout)."""
+    rng = np.random.default_rng(12)
+    H1, H2 = 0, 1                     # heads of 70,000 and 65,535 in-edges
+    n = 72000
+    edges, w = [], []
+    for u in range(2, 70002):
+        edges.append((u, H1))
+    w += list(rng.uniform(0, 1, 70000) * (0.9 / 35000.0))       # ~0.9 in all, uneven
+    for u in range(2, 65537):
+        edges.append((u, H2))
+    w += list(rng.uniform(0, 1, 65535) * (0.95 / 32767.5))
+    for u in range(2, n):
+        # every tail gets back to a head, and some have many in-edges
+        extra = 300 if u % 97 == 0 else 0
+        srcs = [H1, H2] + [int(x) for x in rng.integers(2, n, extra)]
+        srcs = sorted(set(srcs) - {u})
+        ww = rng.uniform(0.1, 1, len(srcs))
+        ww = ww / ww.sum() * 0.97
+        edges += [(t, u) for t in srcs]
+        w += list(ww)
+    g = edges_to_graph(n, edges, [float(x) for x in w], LT)
+    ctx = new_ctx(imm, g)
+    o = check_stream(imm, ctx, g, 4000, 13)
+    for k in (1, 10):
+        s1, c1 = imm.imm_select(ctx, k)
+        s2, c2 = o.select(k)
+        assert np.array_equal(s1, s2) and c1 == c2
+
+
 def test_stream_extension_is_prefix_stable(imm, large_path):
     g = graphgen.make_graph(2048, 16384, 21, IC, "uniform", pmax=0.2)
     a = new_ctx(imm, g)
