@@ -144,8 +144,6 @@ struct imm_ctx {
     BatchOut fo{};
     uint32_t fb_large = 0;
     struct Pinned {
-        uint32_t large_count;
-        uint32_t long_count;
         uint32_t k;
         BatchScalars sc;
         SelectState state;
@@ -762,8 +760,8 @@ int batch_phase1(imm_ctx* c, uint64_t theta)
     if (c->model == IMM_IC) CK(launch_ic_small(g, b, c->di, c->stream));
     else CK(launch_lt_small(g, b, ms, c->di, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
-    CK(cudaMemcpyAsync(&c->pin->large_count, &sc->large_count, 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&c->pin->long_count, &sc->long_count, 4, cudaMemcpyDeviceToHost, c->stream));
+    // the batch scalars in one read-back: phase 2 needs the hand-off counts
+    CK(cudaMemcpyAsync(&c->pin->sc, sc, sizeof(BatchScalars), cudaMemcpyDeviceToHost, c->stream));
     c->acc_sample_launches += 1;
     c->acc_launches += 1;
     return IMM_OK;
@@ -773,8 +771,8 @@ int batch_phase2(imm_ctx* c)
 {
     c->acc_sample_ms += elapsed(c, 0, 1);
     SampleBatch& b = c->fb;
-    const uint32_t large_count = c->pin->large_count;
-    const uint32_t long_count = c->pin->long_count;  // LT walks already bound for the bitmap slots
+    const uint32_t large_count = c->pin->sc.large_count;
+    const uint32_t long_count = c->pin->sc.long_count;  // LT walks already bound for the bitmap slots
     const uint32_t words = b.words;
     c->fb_large = large_count + long_count;
     if (large_count + long_count) {
