@@ -2079,12 +2079,25 @@ extern "C" int imm_run_batch(const imm_query* queries, uint32_t nq, uint32_t* se
     const double t_setup = ms_since(tb0);
     const auto tb1 = std::chrono::steady_clock::now();
     {
+        // the queries go in two cohorts one wave apart: while one cohort's
+        // batched selection runs, the other samples (in one cohort every
+        // query would wait for the selection before sampling again)
+        std::vector<Job*> later;
+        if (active.size() >= 8) {
+            std::vector<Job*> first;
+            for (size_t t = 0; t < active.size(); ++t) (t % 2 ? later : first).push_back(active[t]);
+            active.swap(first);
+        }
         WaveState ws;
         while (rc == IMM_OK) {
-            bool any = false;
+            bool any = !later.empty();
             for (Job* j : active) any = any || (j->stage < 4);
             if (!any) break;
             rc = run_wave(active, g0, g0->stream, &launches, ws);
+            if (!later.empty()) {
+                active.insert(active.end(), later.begin(), later.end());
+                later.clear();
+            }
         }
         // nothing may still run on the workers' buffers when they are freed
         cudaStreamSynchronize(g0->stream);
